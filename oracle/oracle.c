@@ -1,0 +1,310 @@
+/*
+ * Plain fp64 CPU oracle for the 25-point acoustic-isotropic wave step with a
+ * PML boundary (arXiv 2009.04619, section III-A).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path.  Shares no code
+ * with the CUDA library.  Written for a reader checking it against the paper:
+ * no blocking, fusion or reordering beyond what the equations state.
+ *
+ * Readings of passages the paper leaves open (each listed in the design
+ * notes):
+ *  - Laplacian coefficients (section III-A, Eq. 3 names them c_xyz, c_xm,
+ *    c_ym, c_zm without values): the standard 8th-order central
+ *    second-derivative weights, c_xm = w_m / dx^2 and
+ *    c_xyz = w_0 (1/dx^2 + 1/dy^2 + 1/dz^2).
+ *  - Time recurrence (Eq. 2, Algorithm 1): the step with index n maps
+ *    (u^{n-1}, u^n) to u^{n+1}; u^0 = u^{-1} = 0; the source term of Eq. 2's
+ *    right-hand side, dt^2 V^2 f^n, is added into u^{n+1}.
+ *  - Source f = w(t) delta(x - x_s): one grid point, amplitude w / (dx dy dz).
+ *  - PML (section III-A names a PML and a 7-point stencil on an eta array
+ *    with halo 1, section IV; no formulas): single isotropic complex stretch
+ *    s = 1 + eta / (i omega), giving
+ *        u_tt + 2 eta u_t + eta^2 u = V^2 (lap u + phi),
+ *        phi_t + eta phi = - grad(eta) . grad(u),
+ *    discretised with centred u_t, backward-Euler damping on phi and 2nd
+ *    order central differences (the 7-point star) for both gradients.
+ *    eta = eta_x(i) + eta_y(j) + eta_z(k), eta_a = eta_max (d / nb)^2 with d
+ *    the distance in points into the layer, eta_max = -3 vmax ln(r0)/(2 nb h).
+ *    The PML update is applied at computed points outside the inner box; the
+ *    inner box uses Eq. 2 unchanged.
+ *  - Outside the computed domain u = 0 (zero halo, never written).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define R ORA_H
+
+static int ext_x(const ora_grid *g) { return g->nx + 2 * g->nb; }
+static int ext_y(const ora_grid *g) { return g->ny + 2 * g->nb; }
+static int ext_z(const ora_grid *g) { return g->nz + 2 * g->nb; }
+
+size_t ora_field_len(const ora_grid *g)
+{
+    return (size_t)(ext_x(g) + 2 * R) * (size_t)(ext_y(g) + 2 * R) * (size_t)(ext_z(g) + 2 * R);
+}
+
+/* Flat index of computed point (i, j, k); -R <= i < Nx + R etc.  x is the
+ * innermost (fastest) dimension, as the paper stores the grid (section IV-A). */
+long ora_index(const ora_grid *g, int i, int j, int k)
+{
+    long sx = ext_x(g) + 2 * R, sy = ext_y(g) + 2 * R;
+    return ((long)(k + R) * sy + (j + R)) * sx + (i + R);
+}
+
+/* Central second-derivative weights of order 2M (Fornberg's closed form):
+ *   w_m = 2 (-1)^{m+1} (M!)^2 / (m^2 (M-m)! (M+m)!),  w_0 = -2 sum_m w_m.
+ * For M = 4 these are the coefficients of the 8th-order, radius-4 stencil of
+ * section III-A. */
+void ora_fd2_weights(int M, double *w)
+{
+    double fM = 1.0;
+    for (int q = 2; q <= M; ++q) fM *= q;
+    double s = 0.0;
+    for (int m = 1; m <= M; ++m) {
+        double a = 1.0, b = 1.0;
+        for (int q = 2; q <= M - m; ++q) a *= q;
+        for (int q = 2; q <= M + m; ++q) b *= q;
+        double sign = (m % 2 == 1) ? 1.0 : -1.0;
+        w[m] = 2.0 * sign * fM * fM / ((double)m * m * a * b);
+        s += w[m];
+    }
+    w[0] = -2.0 * s;
+}
+
+/* Coefficients of the 25-point Laplacian, section III-A (Eq. 3). */
+void ora_laplacian_coeffs(const ora_grid *g, double *c0, double *cx, double *cy, double *cz)
+{
+    double w[R + 1];
+    ora_fd2_weights(R, w);
+    double ix = 1.0 / (g->dx * g->dx), iy = 1.0 / (g->dy * g->dy), iz = 1.0 / (g->dz * g->dz);
+    *c0 = w[0] * (ix + iy + iz);
+    cx[0] = cy[0] = cz[0] = 0.0;
+    for (int m = 1; m <= R; ++m) {
+        cx[m] = w[m] * ix;
+        cy[m] = w[m] * iy;
+        cz[m] = w[m] * iz;
+    }
+}
+
+/* Von Neumann limit of the leapfrog step of Eq. 2 with the Laplacian above:
+ * the amplification stays on the unit circle while dt^2 V^2 max|symbol| <= 4.
+ * The 1D symbol -(w_0 + 2 sum_m w_m cos(m theta)) peaks at theta = pi. */
+double ora_cfl_dt(double vmax, double dx, double dy, double dz)
+{
+    double w[R + 1];
+    ora_fd2_weights(R, w);
+    double S = w[0];
+    for (int m = 1; m <= R; ++m) S += 2.0 * w[m] * ((m % 2) ? -1.0 : 1.0);
+    S = fabs(S);
+    double sum = S * (1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz));
+    return 2.0 / (vmax * sqrt(sum));
+}
+
+/* Distance (points) of index i into the PML along one axis: 0 inside
+ * [nb, nb + n_inner), growing by one per point outward on either side. */
+static int pml_depth(int n_inner, int nb, int i)
+{
+    int d = 0;
+    if (nb - i > d) d = nb - i;
+    if (i - (nb + n_inner - 1) > d) d = i - (nb + n_inner - 1);
+    return d;
+}
+
+double ora_eta_max(const ora_grid *g, double h)
+{
+    if (g->nb <= 0) return 0.0;
+    return -3.0 * g->vmax * log(g->r0) / (2.0 * g->nb * h);
+}
+
+/* Damping profile along one axis: eta_max (d / nb)^2. */
+double ora_eta_axis(int n_inner, int nb, double eta_max, int i)
+{
+    if (nb <= 0) return 0.0;
+    double d = (double)pml_depth(n_inner, nb, i);
+    return eta_max * (d / nb) * (d / nb);
+}
+
+/* The eta array of section IV-A (3D blocking using shared memory for the
+ * boundary regions): eta_x(i) + eta_y(j) + eta_z(k), defined on the computed
+ * domain and its halo. */
+void ora_eta(const ora_grid *g, double *eta)
+{
+    double ex = ora_eta_max(g, g->dx), ey = ora_eta_max(g, g->dy), ez = ora_eta_max(g, g->dz);
+    for (int k = -R; k < ext_z(g) + R; ++k)
+        for (int j = -R; j < ext_y(g) + R; ++j)
+            for (int i = -R; i < ext_x(g) + R; ++i)
+                eta[ora_index(g, i, j, k)] = ora_eta_axis(g->nx, g->nb, ex, i) +
+                                             ora_eta_axis(g->ny, g->nb, ey, j) +
+                                             ora_eta_axis(g->nz, g->nb, ez, k);
+}
+
+/* A computed point lies in the PML when it is outside the inner box
+ * (section III-B). */
+int ora_is_pml(const ora_grid *g, int i, int j, int k)
+{
+    return pml_depth(g->nx, g->nb, i) > 0 || pml_depth(g->ny, g->nb, j) > 0 ||
+           pml_depth(g->nz, g->nb, k) > 0;
+}
+
+/* The seven-region decomposition of section III-B (Fig. 1): 0 inner,
+ * 1 top / 2 bottom (full x and y, cut along z), 3 front / 4 back (full x,
+ * inner z, cut along y), 5 left / 6 right (inner y and z, cut along x). */
+int ora_region(const ora_grid *g, int i, int j, int k)
+{
+    int nb = g->nb;
+    if (k < nb) return 1;
+    if (k >= nb + g->nz) return 2;
+    if (j < nb) return 3;
+    if (j >= nb + g->ny) return 4;
+    if (i < nb) return 5;
+    if (i >= nb + g->nx) return 6;
+    return 0;
+}
+
+static int pick_threads(int nthreads)
+{
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+/* 25-point star Laplacian at every computed point (section III-A, Eq. 3). */
+void ora_laplacian(const ora_grid *g, const double *u, double *lap, int nthreads)
+{
+    double c0, cx[R + 1], cy[R + 1], cz[R + 1];
+    ora_laplacian_coeffs(g, &c0, cx, cy, cz);
+    long sx = ext_x(g) + 2 * R, sxy = sx * (ext_y(g) + 2 * R);
+    int Nx = ext_x(g), Ny = ext_y(g), Nz = ext_z(g);
+    int nth = pick_threads(nthreads);
+#pragma omp parallel for num_threads(nth) schedule(static)
+    for (int k = 0; k < Nz; ++k)
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                long p = ora_index(g, i, j, k);
+                double L = c0 * u[p];
+                for (int m = 1; m <= R; ++m)
+                    L += cx[m] * (u[p + m] + u[p - m]) + cy[m] * (u[p + m * sx] + u[p - m * sx]) +
+                         cz[m] * (u[p + m * sxy] + u[p - m * sxy]);
+                lap[p] = L;
+            }
+}
+
+/* One time step (Eq. 2 in the inner region, the PML reading above outside):
+ * writes u^{n+1} and phi^{n+1} at every computed point.  m = V^2 dt^2. */
+void ora_step(const ora_grid *g, const double *m, const double *eta, const double *u_prev,
+              const double *u_cur, const double *phi_cur, double *u_next, double *phi_next,
+              int nthreads)
+{
+    double c0, cx[R + 1], cy[R + 1], cz[R + 1];
+    ora_laplacian_coeffs(g, &c0, cx, cy, cz);
+    long sx = ext_x(g) + 2 * R, sxy = sx * (ext_y(g) + 2 * R);
+    int Nx = ext_x(g), Ny = ext_y(g), Nz = ext_z(g);
+    double dt = g->dt;
+    int nth = pick_threads(nthreads);
+#pragma omp parallel for num_threads(nth) schedule(static)
+    for (int k = 0; k < Nz; ++k)
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                long p = ora_index(g, i, j, k);
+                const double *u = u_cur;
+                double L = c0 * u[p];
+                for (int mm = 1; mm <= R; ++mm)
+                    L += cx[mm] * (u[p + mm] + u[p - mm]) +
+                         cy[mm] * (u[p + mm * sx] + u[p - mm * sx]) +
+                         cz[mm] * (u[p + mm * sxy] + u[p - mm * sxy]);
+                if (!ora_is_pml(g, i, j, k)) {
+                    /* Eq. 2: u^{n+1} = (2 + dt^2 V^2 lap) u^n - u^{n-1} */
+                    u_next[p] = 2.0 * u[p] - u_prev[p] + m[p] * L;
+                    phi_next[p] = phi_cur[p];
+                } else {
+                    double e = eta[p] * dt;
+                    /* grad(eta) . grad(u) with 2nd-order central differences
+                     * (the 7-point star on eta, halo 1). */
+                    double gx = (eta[p + 1] - eta[p - 1]) / (2.0 * g->dx) *
+                                ((u[p + 1] - u[p - 1]) / (2.0 * g->dx));
+                    double gy = (eta[p + sx] - eta[p - sx]) / (2.0 * g->dy) *
+                                ((u[p + sx] - u[p - sx]) / (2.0 * g->dy));
+                    double gz = (eta[p + sxy] - eta[p - sxy]) / (2.0 * g->dz) *
+                                ((u[p + sxy] - u[p - sxy]) / (2.0 * g->dz));
+                    double ph = phi_cur[p];
+                    u_next[p] = ((2.0 - e * e) * u[p] - (1.0 - e) * u_prev[p] + m[p] * (L + ph)) /
+                                (1.0 + e);
+                    phi_next[p] = (ph - dt * (gx + gy + gz)) / (1.0 + e);
+                }
+            }
+}
+
+/* Algorithm 1: the time loop with source injection, plus receiver sampling
+ * of u^{n+1} after injection.  Inputs are the fp32 values the GPU sees,
+ * widened to double; m = v^2 dt^2 is formed in double.
+ *   velocity: Nz*Ny*Nx floats (computed domain, x fastest)
+ *   wavelet:  nt floats, w(n dt)
+ *   traces:   nt*nrec doubles, traces[n*nrec + r] = u^{n+1}(rec_r)
+ *   u_final, u_prev_final, phi_final: Nz*Ny*Nx doubles or NULL.
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int ora_run_shot(const ora_grid *g, const float *velocity, const float *wavelet, int nt,
+                 const int *src_ijk, const int *rec_ijk, int nrec, double *traces,
+                 double *u_final, double *u_prev_final, double *phi_final, int nthreads)
+{
+    int Nx = ext_x(g), Ny = ext_y(g), Nz = ext_z(g);
+    if (Nx <= 0 || Ny <= 0 || Nz <= 0 || nt < 0) return -1;
+    size_t n = ora_field_len(g);
+    double *buf = (double *)calloc(6 * n, sizeof(double));
+    if (!buf) return -1;
+    double *m = buf, *eta = buf + n, *u0 = buf + 2 * n, *u1 = buf + 3 * n, *u2 = buf + 4 * n,
+           *phi = buf + 5 * n;
+    double *phi_next = (double *)calloc(n, sizeof(double));
+    if (!phi_next) {
+        free(buf);
+        return -1;
+    }
+    double dt = g->dt;
+    for (int k = 0; k < Nz; ++k)
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                double v = (double)velocity[((size_t)k * Ny + j) * Nx + i];
+                m[ora_index(g, i, j, k)] = v * v * dt * dt;
+            }
+    ora_eta(g, eta);
+    double inv_vol = 1.0 / (g->dx * g->dy * g->dz);
+    long ps = src_ijk ? ora_index(g, src_ijk[0], src_ijk[1], src_ijk[2]) : -1;
+    double *u_prev = u0, *u_cur = u1, *u_next = u2;
+    for (int step = 0; step < nt; ++step) {
+        ora_step(g, m, eta, u_prev, u_cur, phi, u_next, phi_next, nthreads);
+        if (ps >= 0) u_next[ps] += m[ps] * (double)wavelet[step] * inv_vol; /* Eq. 2 RHS */
+        for (int r = 0; r < nrec; ++r)
+            traces[(size_t)step * nrec + r] =
+                u_next[ora_index(g, rec_ijk[3 * r], rec_ijk[3 * r + 1], rec_ijk[3 * r + 2])];
+        double *t = u_prev;
+        u_prev = u_cur;
+        u_cur = u_next;
+        u_next = t;
+        t = phi;
+        phi = phi_next;
+        phi_next = t;
+    }
+    for (int k = 0; k < Nz; ++k)
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                size_t c = ((size_t)k * Ny + j) * Nx + i;
+                long p = ora_index(g, i, j, k);
+                if (u_final) u_final[c] = u_cur[p];
+                if (u_prev_final) u_prev_final[c] = u_prev[p];
+                if (phi_final) phi_final[c] = phi[p];
+            }
+    /* phi and phi_next may have swapped: free whichever pointer is not in buf */
+    if (phi == buf + 5 * n) free(phi_next);
+    else free(phi);
+    free(buf);
+    return 0;
+}
