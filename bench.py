@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Throughput of the fused 25-point wave step (Gpoint-updates/s, % of HBM roofline).
+
+One bench step = one whole shot of the 512^3 workload (448^3 inner region +
+32-point PML, layered velocity model, 10 Hz Ricker source, 12,544 surface
+receivers, 1000 time steps) through ``run_shot`` of the C ABI: every row of
+the hot path (interior update, fused PML, source injection, receiver
+sampling, the time loop) runs in each step.  Inputs are resident in HBM when
+the timed region starts; each of the four fields (u^n, u^{n-1}, m, phi) is
+~571 MB, far above the 129 MB L2, so no L2 flush is needed between steps.
+
+--impl reference times the fp64 CPU oracle on the host cores on bounded
+samples of the same workload.  Under torchrun every rank runs its own
+replica shot (shots are independent: weak scaling, no collective on the data
+path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "25-pt stencil Gpoint-updates/s"
+UNIT = "Gpt/s"
+HBM_FALLBACK_GBS = 6800.0
+
+# DRAM bytes per launch of the step kernel measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the sha256 of the
+# kernel source it was measured on; a changed kernel reports null.
+NCU_TRAFFIC = {}
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["seisgb", "reference"], default="seisgb")
+    p.add_argument("--no-cpu-baseline", action="store_true",
+                   help="skip the oracle CPU-baseline leg (profiling runs)")
+    p.add_argument("--roofline-launches", type=int, default=100)
+    p.add_argument("--oracle-steps", type=int, default=6,
+                   help="time steps per oracle sample (CPU baseline / reference arm)")
+    return p.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload():
+    from paper_2009_04619_gb300 import synth
+    return synth.LARGE
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("step_kernel.cuh", "ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2009_04619_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def _alg_bytes_per_launch(w):
+    """Compulsory bytes of one step: read u^n, u^{n-1}, m and write u^{n+1}
+    (16 B per point, fp32) plus phi read + write (8 B) at PML points."""
+    N = w.points
+    inner = w.nx * w.ny * w.nz
+    return 16 * N + 8 * (N - inner)
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.uuid], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _time_oracle(w, vel, wav, src, rec, steps, nthreads):
+    """Seconds for `steps` oracle time steps of workload w (oracle set-up time of
+    the same call with zero steps subtracted)."""
+    import oracle
+    vmax = float(vel.max())
+    dt = float(np.float32(w.cfl_fraction * oracle.cfl_dt(vmax, w.h, w.h, w.h)))
+    g = oracle.Grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax=vmax,
+                    r0=float(np.float32(1e-3)))
+    t = time.perf_counter()
+    oracle.run_shot(g, vel, wav, 0, src, rec, nthreads=nthreads, want_state=False)
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.run_shot(g, vel, wav, steps, src, rec, nthreads=nthreads, want_state=False)
+    ts = time.perf_counter() - t
+    return max(ts - t0, 1e-9), ts, t0
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    w = _workload()
+    vel = w.velocity()
+    from paper_2009_04619_gb300 import synth
+    import oracle
+    oracle.build()
+    vmax = float(vel.max())
+    dt = float(np.float32(w.cfl_fraction * oracle.cfl_dt(vmax, w.h, w.h, w.h)))
+    wav = synth.ricker(w.nt, dt, w.fp)
+    rec = w.receivers()
+    cores = os.cpu_count() or 1
+    S = a.oracle_steps
+    for _ in range(a.warmup):
+        _time_oracle(w, vel, wav, w.source(), rec, 1, cores)
+    tot = 0.0
+    for _ in range(a.steps):
+        dt_s, _, _ = _time_oracle(w, vel, wav, w.source(), rec, S, cores)
+        tot += dt_s
+    pts = w.points * S * a.steps
+    val = pts / tot / 1e9
+    sample = (f"{S} of {w.nt} time steps of the {w.name} workload per bench step "
+              f"(oracle set-up time subtracted), fp64 oracle, {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot / a.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape), "nb": w.nb,
+                                        "nt_sampled": S},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2009_04619_gb300 import build, seisgb, synth
+    build.build()
+    seisgb.lib()
+    w = _workload()
+    vel = w.velocity()
+    vmax = float(vel.max())
+    g0 = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, 1.0, vmax)
+    dt = float(np.float32(w.cfl_fraction * seisgb.cfl_dt(g0, vmax)))
+    g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax)
+    wav = synth.ricker(w.nt, dt, w.fp)
+    src = w.source()
+    rec = w.receivers()
+    nrec = rec.shape[0]
+    d_v = torch.from_numpy(vel).to(dev)
+    d_w = torch.from_numpy(wav).to(dev)
+    d_tr = torch.zeros((w.nt, nrec), dtype=torch.float32, device=dev)
+
+    for _ in range(a.warmup):
+        seisgb.run_shot(g, d_v, d_w, w.nt, src, rec, d_tr)
+
+    uuid = torch.cuda.get_device_properties(dev).uuid
+    uuid = "GPU-" + str(uuid) if not str(uuid).startswith("GPU-") else str(uuid)
+    clocks = ClockSampler(uuid)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.3)
+    seisgb.launch_count(reset=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(a.steps):
+        seisgb.run_shot(g, d_v, d_w, w.nt, src, rec, d_tr)
+    e1.record(stream)
+    barrier()
+    launches = seisgb.launch_count(reset=True)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / a.steps
+    value = w.points * w.nt * a.steps * world / (ms / 1e3) / 1e9
+
+    # dominant kernel: back-to-back fused steps on the same grid, CUDA events on
+    # the launching stream
+    L = seisgb.layout(g)
+    bufs = [torch.zeros(int(L.elems), dtype=torch.float32, device=dev) for _ in range(3)]
+    d_m = torch.zeros(int(L.elems), dtype=torch.float32, device=dev)
+    seisgb.pack(g, (d_v * dt) ** 2, d_m)
+    M = a.roofline_launches
+    for n in range(3):
+        seisgb.stencil_step(g, bufs[n % 2], bufs[(n + 1) % 2], d_m, bufs[2], n, source=(*src, d_w))
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for n in range(M):
+        seisgb.stencil_step(g, bufs[n % 2], bufs[(n + 1) % 2], d_m, bufs[2], n % w.nt,
+                            source=(*src, d_w))
+    r1.record(stream)
+    torch.cuda.synchronize()
+    kern_ms = r0.elapsed_time(r1) / M
+    alg = _alg_bytes_per_launch(w)
+    peak, peak_kind = _peaks()
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC.get(_kernel_hash())
+    del bufs, d_m
+
+    # end to end through the C ABI with pinned host buffers: velocity and wavelet
+    # copied in, traces copied out, every step
+    h_v = torch.from_numpy(vel).pin_memory()
+    h_w = torch.from_numpy(wav).pin_memory()
+    h_tr = torch.zeros((w.nt, nrec), dtype=torch.float32).pin_memory()
+    seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
+    barrier()
+    e2e_s = time.perf_counter() - t
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_val = w.points * w.nt * a.steps * world / e2e_s / 1e9
+    h2d = vel.nbytes + wav.nbytes + rec.nbytes + 12
+    d2h = w.nt * nrec * 4
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "grid": list(w.shape), "inner": [w.nz, w.ny, w.nx],
+                   "nb": w.nb, "nt": w.nt, "nrec": nrec, "dt": dt,
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (4 fields x 571 MB), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "fused_step_kernel", "kernel_ms": kern_ms,
+                     "alg_bytes_per_launch": alg, "peak_source": peak_kind,
+                     "step_ms_in_shot": ms_per_step / w.nt},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        S = a.oracle_steps
+        dt_s, ts, t0 = _time_oracle(w, vel, wav, src, rec, S, cores)
+        out["cpu_baseline"] = {
+            "value": w.points * S / dt_s / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{S} of {w.nt} time steps of the {w.name} workload "
+                       f"({ts:.1f} s call minus {t0:.1f} s oracle set-up), fp64, {cores} threads")}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

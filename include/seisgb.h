@@ -1,0 +1,147 @@
+/*
+ * seisgb: GB300 (sm_103a) library for the 3D acoustic-isotropic wave equation
+ * with an 8th-order, 25-point star Laplacian and a fused PML boundary
+ * (Sai, Mellor-Crummey, Meng, Araya-Polo, Meng, "Accelerating High-Order
+ * Stencils on GPUs", arXiv 2009.04619).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Coordinates (i, j, k) index the computed domain, x fastest, z = depth
+ *    (section IV-A stores the grid as a flat array with X innermost).  The
+ *    computed domain is the inner region (nx, ny, nz) plus a PML of nb points
+ *    on each side (section III-B): Nx = nx + 2 nb, likewise Ny, Nz.
+ *  - Fields passed to stencil_step live in the padded layout reported by
+ *    sgb_layout: a zero halo around the computed domain (8 points on the low x
+ *    side, at least 4 elsewhere), rows padded to a multiple of 32 elements.
+ *    The halo must hold zeros and is never written.
+ *  - Every call returns SGB_OK (0) or a negative SGB_ERR_* code.  Arguments
+ *    are validated before any GPU work is enqueued, so a rejected call leaves
+ *    no partial state.  sgb_last_error() gives a message for the calling
+ *    thread's most recent failure.
+ *  - Device pointers are owned by the caller; the library never frees them.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default).
+ */
+#ifndef SEISGB_H
+#define SEISGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGB_OK 0
+#define SGB_PENDING 1
+#define SGB_ERR_INVALID_ARG (-1)
+#define SGB_ERR_OUT_OF_MEMORY (-2)
+#define SGB_ERR_UNSTABLE_DT (-3)
+#define SGB_ERR_CUDA (-4)
+#define SGB_ERR_TIMEOUT (-5)
+#define SGB_ERR_NONFINITE (-6)
+#define SGB_ERR_REJECTED (-7)
+
+/* Wavefield storage formats (arithmetic is always fp32). */
+#define SGB_FP32 0
+#define SGB_FP16_SCALED 1
+#define SGB_BF16 2
+
+/* Problem statement (section III-B: inner-region size and PML width are
+ * inputs; Eq. 2: spacing and dt). */
+typedef struct {
+    int32_t nx, ny, nz;  /* inner-region points, each >= 1 */
+    int32_t nb;          /* PML width per side in points, >= 0 (0: zero walls) */
+    float dx, dy, dz;    /* grid spacing, metres, > 0 */
+    float dt;            /* time step, seconds, > 0 */
+    float vmax;          /* velocity (m/s) that sets the PML damping strength
+                            eta_max = -3 vmax ln(pml_r0) / (2 nb h); normally
+                            the model's maximum velocity */
+    float pml_r0;        /* PML target reflection coefficient in (0, 1];
+                            1 switches the damping off */
+    int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED or SGB_BF16 */
+} sgb_grid;
+
+/* Padded device layout of one field (element counts; multiply by the element
+ * size for bytes). */
+typedef struct {
+    int32_t Nx, Ny, Nz;   /* computed extents */
+    int32_t halo_lo_x;    /* zero points before computed x = 0 (8) */
+    int32_t halo;         /* zero points before y = 0 and z = 0 (4) */
+    int64_t sx, sy, sz;   /* padded extents: row pitch, rows per plane, planes */
+    int64_t stride_y;     /* = sx */
+    int64_t stride_z;     /* = sx * sy */
+    int64_t origin;       /* element offset of computed point (0, 0, 0) */
+    int64_t elems;        /* elements per field = sx * sy * sz */
+} sgb_layout_info;
+
+/* Point source: f = w(t) delta(x - x_s), added into u^{n+1} as
+ * m(x_s) w(n dt) / (dx dy dz) (Eq. 2 right-hand side, Algorithm 1). */
+typedef struct {
+    int32_t i, j, k;        /* computed coordinates, inside the inner region */
+    const float *wavelet;   /* device array of w(n dt); element [step] is used */
+} sgb_source;
+
+/* Receivers sample u^{n+1} after source injection. */
+typedef struct {
+    int32_t nrec;
+    const int32_t *ijk;     /* HOST array nrec x 3 of computed coordinates */
+    float *traces;          /* device array of nrec floats receiving the samples */
+} sgb_receivers;
+
+/* Fill *out with the padded layout of g.  INVALID_ARG on bad extents. */
+int sgb_layout(const sgb_grid *g, sgb_layout_info *out);
+
+/* Largest stable dt for velocities up to vmax: the von Neumann limit of the
+ * leapfrog step of Eq. 2 with the 25-point Laplacian,
+ * 2 / (vmax sqrt((2048/315) (dx^-2 + dy^-2 + dz^-2))). */
+int sgb_cfl_dt(const sgb_grid *g, float vmax, float *dt_max);
+
+/* One time step (Eq. 2 in the inner region, the PML update outside it, one
+ * launch).  Reads u_cur = u^n and u_prev_to_next = u^{n-1}; overwrites
+ * u_prev_to_next with u^{n+1} (the update is pointwise in u^{n-1}, so this is
+ * safe).  m = V^2 dt^2 (fp32, padded layout).  phi: the PML auxiliary field,
+ * fp32 padded layout, read and written at PML points only (start from zeros).
+ * u fields are fp32 (storage SGB_FP32).  step selects src->wavelet[step].
+ * src and rec may be NULL.  All device pointers must be 16-byte aligned.
+ * Asynchronous on stream.  UNSTABLE_DT when g->dt exceeds the CFL limit for
+ * g->vmax. */
+int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next, const float *m,
+                 float *phi, int32_t step, const sgb_source *src, const sgb_receivers *rec,
+                 void *stream);
+
+/* A whole shot (Algorithm 1): u^0 = u^{-1} = 0, nt steps, source injection and
+ * receiver sampling every step.
+ *   velocity  Nz*Ny*Nx fp32 compact (x fastest), host or device
+ *   wavelet   nt fp32, host or device
+ *   src_ijk   host int32[3] (NULL: no source)
+ *   rec_ijk   host int32[nrec*3]
+ *   traces    nt*nrec fp32, host or device; traces[n*nrec + r] = u^{n+1}(rec_r)
+ *   final_u   Nz*Ny*Nx fp32 compact u^{nt}, host or device, or NULL
+ * Scratch (two wavefields, phi, m) comes from a library-owned stream-ordered
+ * pool and is released before returning.  Enqueued on stream, then the call
+ * waits for the stream.  UNSTABLE_DT if dt exceeds the CFL limit of the
+ * model's actual maximum velocity; NONFINITE if a receiver saw a NaN/Inf. */
+int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
+             const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
+             float *final_u, void *stream);
+
+/* Layout conversion between compact (Nz, Ny, Nx) fp32 arrays and the padded
+ * layout (device pointers; pack zeroes the halo).  Asynchronous on stream. */
+int sgb_pack(const sgb_grid *g, const float *compact, float *padded, void *stream);
+int sgb_unpack(const sgb_grid *g, const float *padded, float *compact, void *stream);
+
+/* Reads (and clears) the device-side error word that kernels set when a
+ * bounded wait gave up or an input was out of range; synchronises stream.
+ * Returns SGB_OK, SGB_ERR_TIMEOUT or SGB_ERR_CUDA. */
+int sgb_device_status(void *stream);
+
+/* Number of this library's kernels launched by the calling thread since the
+ * last reset (graph replays count every kernel node). */
+int64_t sgb_launch_count(int reset);
+
+/* Message for the calling thread's most recent error ("" if none). */
+const char *sgb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEISGB_H */

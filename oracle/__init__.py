@@ -76,6 +76,7 @@ def lib():
         L.ora_step.argtypes = [gp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         fp = ctypes.POINTER(ctypes.c_float)
         ip = ctypes.POINTER(ctypes.c_int)
+        L.ora_step_points.argtypes = [gp, fp, fp, fp, fp, ip, ctypes.c_int, dp, dp, ctypes.c_int]
         L.ora_run_shot.argtypes = [gp, fp, fp, ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, dp, dp,
                                    ctypes.c_int]
         L.ora_run_shot.restype = ctypes.c_int
@@ -196,6 +197,20 @@ def step(g: Grid, m, u_prev, u_cur, phi_cur, nthreads: int = 0):
     lib().ora_step(ctypes.byref(g.c()), _ptr(mf), _ptr(e), _ptr(up), _ptr(uc), _ptr(ph),
                    _ptr(un), _ptr(pn), nthreads)
     return unpad(un), unpad(pn)
+
+
+def step_points(g: Grid, m, u_prev, u_cur, phi, pts, nthreads: int = 0):
+    """One step evaluated only at the listed points (int [npts, 3] rows (i, j, k)),
+    reading float32 compact fields; returns (u_next, phi_next) at those points."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (m, u_prev, u_cur, phi)]
+    for a in arrs:
+        assert a.shape == g.shape
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.int32).reshape(-1, 3))
+    n = pts.shape[0]
+    ou, op = np.zeros(n), np.zeros(n)
+    lib().ora_step_points(ctypes.byref(g.c()), *(_ptr(a, ctypes.c_float) for a in arrs),
+                          _ptr(pts, ctypes.c_int), n, _ptr(ou), _ptr(op), nthreads)
+    return ou, op
 
 
 def run_shot(g: Grid, velocity: np.ndarray, wavelet: np.ndarray, nt: int, src, rec,

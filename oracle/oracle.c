@@ -199,8 +199,49 @@ void ora_laplacian(const ora_grid *g, const double *u, double *lap, int nthreads
             }
 }
 
-/* One time step (Eq. 2 in the inner region, the PML reading above outside):
- * writes u^{n+1} and phi^{n+1} at every computed point.  m = V^2 dt^2. */
+/* Values one point's update reads: the 25-point star of u^n along each axis
+ * (u[a][R + o] = u^n at offset o on axis a, |o| <= R), eta at offsets -1, 0,
+ * +1 on each axis, and m, u^{n-1}, phi^n at the point. */
+typedef struct {
+    double u[3][2 * R + 1];
+    double eta[3][3];
+    double m, u_prev, phi;
+    int pml;
+} ora_star;
+
+/* One point of one time step: Eq. 2 in the inner region, the PML reading
+ * above outside it.  m = V^2 dt^2. */
+static void star_update(const ora_grid *g, double c0, const double *cx, const double *cy,
+                        const double *cz, const ora_star *s, double *u_next, double *phi_next)
+{
+    const double *cc[3] = {cx, cy, cz};
+    const double h[3] = {g->dx, g->dy, g->dz};
+    double u0 = s->u[0][R];
+    double L = c0 * u0;
+    for (int mm = 1; mm <= R; ++mm)
+        L += cc[0][mm] * (s->u[0][R + mm] + s->u[0][R - mm]) +
+             cc[1][mm] * (s->u[1][R + mm] + s->u[1][R - mm]) +
+             cc[2][mm] * (s->u[2][R + mm] + s->u[2][R - mm]);
+    if (!s->pml) {
+        /* Eq. 2: u^{n+1} = (2 + dt^2 V^2 lap) u^n - u^{n-1} */
+        *u_next = 2.0 * u0 - s->u_prev + s->m * L;
+        *phi_next = s->phi;
+        return;
+    }
+    double dt = g->dt;
+    double e = s->eta[0][1] * dt;
+    /* grad(eta) . grad(u) with 2nd-order central differences (the 7-point star
+     * on eta, halo 1) */
+    double gd[3];
+    for (int ax = 0; ax < 3; ++ax)
+        gd[ax] = (s->eta[ax][2] - s->eta[ax][0]) / (2.0 * h[ax]) *
+                 ((s->u[ax][R + 1] - s->u[ax][R - 1]) / (2.0 * h[ax]));
+    double gsum = gd[0] + gd[1] + gd[2];
+    *u_next = ((2.0 - e * e) * u0 - (1.0 - e) * s->u_prev + s->m * (L + s->phi)) / (1.0 + e);
+    *phi_next = (s->phi - dt * gsum) / (1.0 + e);
+}
+
+/* One time step at every computed point: writes u^{n+1} and phi^{n+1}. */
 void ora_step(const ora_grid *g, const double *m, const double *eta, const double *u_prev,
               const double *u_cur, const double *phi_cur, double *u_next, double *phi_next,
               int nthreads)
@@ -208,40 +249,68 @@ void ora_step(const ora_grid *g, const double *m, const double *eta, const doubl
     double c0, cx[R + 1], cy[R + 1], cz[R + 1];
     ora_laplacian_coeffs(g, &c0, cx, cy, cz);
     long sx = ext_x(g) + 2 * R, sxy = sx * (ext_y(g) + 2 * R);
+    const long st[3] = {1, sx, sxy};
     int Nx = ext_x(g), Ny = ext_y(g), Nz = ext_z(g);
-    double dt = g->dt;
     int nth = pick_threads(nthreads);
 #pragma omp parallel for num_threads(nth) schedule(static)
     for (int k = 0; k < Nz; ++k)
         for (int j = 0; j < Ny; ++j)
             for (int i = 0; i < Nx; ++i) {
                 long p = ora_index(g, i, j, k);
-                const double *u = u_cur;
-                double L = c0 * u[p];
-                for (int mm = 1; mm <= R; ++mm)
-                    L += cx[mm] * (u[p + mm] + u[p - mm]) +
-                         cy[mm] * (u[p + mm * sx] + u[p - mm * sx]) +
-                         cz[mm] * (u[p + mm * sxy] + u[p - mm * sxy]);
-                if (!ora_is_pml(g, i, j, k)) {
-                    /* Eq. 2: u^{n+1} = (2 + dt^2 V^2 lap) u^n - u^{n-1} */
-                    u_next[p] = 2.0 * u[p] - u_prev[p] + m[p] * L;
-                    phi_next[p] = phi_cur[p];
-                } else {
-                    double e = eta[p] * dt;
-                    /* grad(eta) . grad(u) with 2nd-order central differences
-                     * (the 7-point star on eta, halo 1). */
-                    double gx = (eta[p + 1] - eta[p - 1]) / (2.0 * g->dx) *
-                                ((u[p + 1] - u[p - 1]) / (2.0 * g->dx));
-                    double gy = (eta[p + sx] - eta[p - sx]) / (2.0 * g->dy) *
-                                ((u[p + sx] - u[p - sx]) / (2.0 * g->dy));
-                    double gz = (eta[p + sxy] - eta[p - sxy]) / (2.0 * g->dz) *
-                                ((u[p + sxy] - u[p - sxy]) / (2.0 * g->dz));
-                    double ph = phi_cur[p];
-                    u_next[p] = ((2.0 - e * e) * u[p] - (1.0 - e) * u_prev[p] + m[p] * (L + ph)) /
-                                (1.0 + e);
-                    phi_next[p] = (ph - dt * (gx + gy + gz)) / (1.0 + e);
+                ora_star s;
+                for (int ax = 0; ax < 3; ++ax) {
+                    for (int o = -R; o <= R; ++o) s.u[ax][R + o] = u_cur[p + o * st[ax]];
+                    for (int o = -1; o <= 1; ++o) s.eta[ax][o + 1] = eta[p + o * st[ax]];
                 }
+                s.m = m[p];
+                s.u_prev = u_prev[p];
+                s.phi = phi_cur[p];
+                s.pml = ora_is_pml(g, i, j, k);
+                star_update(g, c0, cx, cy, cz, &s, &u_next[p], &phi_next[p]);
             }
+}
+
+/* The same step evaluated at listed points only, reading fp32 compact fields
+ * (Nz*Ny*Nx, x fastest; zero outside the computed domain) and the eta profile
+ * directly.  Lets a test check a full-size GPU step on sampled outputs.
+ * pts: npts triples (i, j, k); out_u / out_phi: npts doubles. */
+void ora_step_points(const ora_grid *g, const float *m, const float *u_prev, const float *u_cur,
+                     const float *phi, const int *pts, int npts, double *out_u, double *out_phi,
+                     int nthreads)
+{
+    double c0, cx[R + 1], cy[R + 1], cz[R + 1];
+    ora_laplacian_coeffs(g, &c0, cx, cy, cz);
+    int N[3] = {ext_x(g), ext_y(g), ext_z(g)};
+    int nin[3] = {g->nx, g->ny, g->nz};
+    double emax[3] = {ora_eta_max(g, g->dx), ora_eta_max(g, g->dy), ora_eta_max(g, g->dz)};
+    int nth = pick_threads(nthreads);
+#pragma omp parallel for num_threads(nth) schedule(static)
+    for (int q = 0; q < npts; ++q) {
+        int c[3] = {pts[3 * q], pts[3 * q + 1], pts[3 * q + 2]};
+        ora_star s;
+        for (int ax = 0; ax < 3; ++ax) {
+            for (int o = -R; o <= R; ++o) {
+                int d[3] = {c[0], c[1], c[2]};
+                d[ax] += o;
+                int inside = d[0] >= 0 && d[0] < N[0] && d[1] >= 0 && d[1] < N[1] && d[2] >= 0 &&
+                             d[2] < N[2];
+                s.u[ax][R + o] =
+                    inside ? (double)u_cur[((size_t)d[2] * N[1] + d[1]) * N[0] + d[0]] : 0.0;
+            }
+            for (int o = -1; o <= 1; ++o) {
+                double e = 0.0;
+                for (int b = 0; b < 3; ++b)
+                    e += ora_eta_axis(nin[b], g->nb, emax[b], c[b] + (b == ax ? o : 0));
+                s.eta[ax][o + 1] = e;
+            }
+        }
+        size_t ci = ((size_t)c[2] * N[1] + c[1]) * N[0] + c[0];
+        s.m = (double)m[ci];
+        s.u_prev = (double)u_prev[ci];
+        s.phi = (double)phi[ci];
+        s.pml = ora_is_pml(g, c[0], c[1], c[2]);
+        star_update(g, c0, cx, cy, cz, &s, &out_u[q], &out_phi[q]);
+    }
 }
 
 /* Algorithm 1: the time loop with source injection, plus receiver sampling

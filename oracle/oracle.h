@@ -59,6 +59,9 @@ void ora_laplacian(const ora_grid *g, const double *u, double *lap, int nthreads
 void ora_step(const ora_grid *g, const double *m, const double *eta,
               const double *u_prev, const double *u_cur, const double *phi_cur,
               double *u_next, double *phi_next, int nthreads);
+void ora_step_points(const ora_grid *g, const float *m, const float *u_prev, const float *u_cur,
+                     const float *phi, const int *pts, int npts, double *out_u, double *out_phi,
+                     int nthreads);
 int ora_run_shot(const ora_grid *g, const float *velocity, const float *wavelet, int nt,
                  const int *src_ijk, const int *rec_ijk, int nrec, double *traces,
                  double *u_final, double *u_prev_final, double *phi_final, int nthreads);

@@ -1,0 +1,129 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+symbol its header declares; host-side validation and layout work on CPU."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2009_04619_gb300 import build, seisgb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for stmt in src.split(";"):
+            stmt = " ".join(stmt.split())
+            if not stmt or stmt.startswith("typedef") or "#" in stmt.split("(")[0]:
+                continue
+            m = re.search(r"(\w+)\s*\([^()]*(\([^()]*\)[^()]*)*\)\s*$", stmt)
+            if m and "{" not in stmt:
+                names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return seisgb.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ("stencil_step", "run_shot", "sgb_layout", "sgb_cfl_dt", "sgb_last_error"):
+        assert n in names, names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding wraps exactly the declared functions
+    assert set(seisgb.SIGNATURES) == names
+
+
+def test_layout_geometry(lib):
+    g = seisgb.make_grid(13, 17, 11, 5, 10, 11, 12, 1e-3, 3000)
+    L = seisgb.layout(g)
+    assert (L.Nx, L.Ny, L.Nz) == (23, 27, 21)
+    assert L.halo_lo_x == 8 and L.halo == 4
+    assert L.sx % 32 == 0 and L.sx >= 8 + 23 + 4
+    assert (L.sy, L.sz) == (27 + 8, 21 + 8)
+    assert L.stride_z == L.sx * L.sy
+    assert L.origin == 4 * L.stride_z + 4 * L.sx + 8
+    assert L.elems == L.sx * L.sy * L.sz
+    assert (L.origin * 4) % 16 == 0 and (L.sx * 4) % 16 == 0
+
+
+def test_cfl_dt_closed_form(lib):
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 7, 12, 1e-3, 3000)
+    got = seisgb.cfl_dt(g, 4500.0)
+    want = 2.0 / (4500.0 * math.sqrt(2048 / 315 * (10 ** -2 + 7 ** -2 + 12 ** -2)))
+    assert math.isclose(got, want, rel_tol=1e-6)
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("nb", -1), ("dx", 0.0), ("dt", -1.0),
+                                         ("pml_r0", 0.0), ("pml_r0", 1.5), ("storage", 7),
+                                         ("vmax", float("nan"))])
+def test_bad_grid_rejected_without_gpu(lib, field, value):
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
+    setattr(g, field, value)
+    with pytest.raises(seisgb.SeisgbError) as e:
+        seisgb.layout(g)
+    assert e.value.code == seisgb.ERR_INVALID_ARG
+
+
+def test_step_argument_checks_precede_any_gpu_work(lib):
+    """Invalid calls return their code from host-side validation alone (these run
+    on a machine without a GPU)."""
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
+    st = 0
+    L = seisgb.lib()
+    buf = (ctypes.c_float * 64)()
+    a = ctypes.addressof(buf)
+    a16 = a + (16 - a % 16) % 16
+    # NULL field
+    assert L.stencil_step(ctypes.byref(g), None, a16, a16, a16, 0, None, None, st) == seisgb.ERR_INVALID_ARG
+    # misaligned pointer
+    assert L.stencil_step(ctypes.byref(g), a16 + 4, a16 + 16, a16, a16, 0, None, None, st) == seisgb.ERR_INVALID_ARG
+    # aliasing u_cur and u_prev_to_next
+    assert L.stencil_step(ctypes.byref(g), a16, a16, a16, a16, 0, None, None, st) == seisgb.ERR_INVALID_ARG
+    # phi required with a PML
+    assert L.stencil_step(ctypes.byref(g), a16, a16 + 16, a16, None, 0, None, None, st) == seisgb.ERR_INVALID_ARG
+    # source outside the inner region
+    src = seisgb.Source(0, 0, 0, a16)
+    assert L.stencil_step(ctypes.byref(g), a16, a16 + 16, a16, a16 + 32, 0, ctypes.byref(src), None, st) == seisgb.ERR_INVALID_ARG
+    # dt above the CFL limit
+    g2 = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1.0, 3000)
+    assert L.stencil_step(ctypes.byref(g2), a16, a16 + 16, a16, a16 + 32, 0, None, None, st) == seisgb.ERR_UNSTABLE_DT
+    assert "CFL" in seisgb.last_error()
+    # negative step
+    assert L.stencil_step(ctypes.byref(g), a16, a16 + 16, a16, a16 + 32, -1, None, None, st) == seisgb.ERR_INVALID_ARG
+
+
+def test_run_shot_argument_checks_without_gpu(lib):
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
+    L = seisgb.lib()
+    v = np.full(g.shape, 2000, np.float32)
+    w = np.zeros(10, np.float32)
+    src = np.array([0, 0, 0], np.int32)  # in the PML: rejected
+    rc = L.run_shot(ctypes.byref(g), v.ctypes.data, w.ctypes.data, 10, src.ctypes.data, None, 0,
+                    None, None, None)
+    assert rc == seisgb.ERR_INVALID_ARG
+    rec = np.array([[5, 5, 1]], np.int32)  # receiver in the PML
+    tr = np.zeros(10, np.float32)
+    src = np.array([5, 5, 5], np.int32)
+    rc = L.run_shot(ctypes.byref(g), v.ctypes.data, w.ctypes.data, 10, src.ctypes.data,
+                    rec.ctypes.data, 1, tr.ctypes.data, None, None)
+    assert rc == seisgb.ERR_INVALID_ARG
+    rc = L.run_shot(ctypes.byref(g), v.ctypes.data, w.ctypes.data, -1, src.ctypes.data, None, 0,
+                    None, None, None)
+    assert rc == seisgb.ERR_INVALID_ARG
