@@ -38,7 +38,10 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per launch of the step kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the sha256 of the
 # kernel source it was measured on; a changed kernel reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu on the 512^3 + 32-point-PML step: 2.19 GB read + 0.664 GB written per launch
+    "374a88a14003529e": 2.854e9,
+}
 
 
 def _args():
@@ -50,7 +53,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="skip the oracle CPU-baseline leg (profiling runs)")
     p.add_argument("--roofline-launches", type=int, default=100)
-    p.add_argument("--oracle-steps", type=int, default=6,
+    p.add_argument("--oracle-steps", type=int, default=40,
                    help="time steps per oracle sample (CPU baseline / reference arm)")
     return p.parse_args()
 
@@ -69,7 +72,7 @@ def _workload():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("step_kernel.cuh", "ptx.cuh"):
+    for f in ("step_kernel.cuh", "ptx.cuh", "step_config.cuh"):
         with open(os.path.join(ROOT, "paper_2009_04619_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -119,4 +119,12 @@ __device__ __forceinline__ void stg128(float *p, float4 v)
                  : "memory");
 }
 
+// 128-bit global store with an L2 cache-policy hint.
+__device__ __forceinline__ void stg128_hint(float *p, float4 v, uint64_t policy)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w), "l"(policy)
+                 : "memory");
+}
+
 }  // namespace sgb

@@ -15,6 +15,7 @@
 #include "../../include/seisgb.h"
 #include "aux_kernels.cuh"
 #include "step_kernel.cuh"
+#include "step_config.cuh"
 
 using namespace sgb;
 
@@ -62,7 +63,7 @@ static __device__ int g_dev_err;
 // ---------------------------------------------------------------------------
 namespace {
 
-using Cfg = TileCfg<16, 8, 2, 8, 4, 2>;  // 64 x 16 tile, 128 threads, 8 + 4 stages
+
 
 struct DevState {
     bool ready = false;
@@ -89,7 +90,7 @@ int device_state(DevState **out)
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)Cfg::SMEM_BYTES));
         CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.occ, fused_step_kernel<Cfg>,
-                                                               Cfg::THREADS, Cfg::SMEM_BYTES));
+                                                               Cfg::BLOCK, Cfg::SMEM_BYTES));
         if (s.occ < 1) return fail(SGB_ERR_CUDA, "step kernel does not fit on an SM");
         CUDA_TRY(cudaGetSymbolAddress((void **)&s.err, g_dev_err));
         cudaMemPoolProps props;
@@ -223,32 +224,6 @@ void fill_step_constants(const sgb_grid *g, const sgb_layout_info &L, StepArgs &
     a.inv_vol = (float)(1.0 / ((double)g->dx * g->dy * g->dz));
 }
 
-// Chunking of z: pick the chunk length that minimises waves x (chunk + priming
-// overhead) for the resident-CTA slots of this GPU.
-void choose_decomposition(const sgb_layout_info &L, const DevState &ds, StepArgs &a, int *grid)
-{
-    a.tiles_x = (L.Nx + Cfg::BX - 1) / Cfg::BX;
-    a.tiles_y = (L.Ny + Cfg::BY - 1) / Cfg::BY;
-    const long long tiles = (long long)a.tiles_x * a.tiles_y;
-    const long long slots = (long long)ds.sms * ds.occ;
-    int best_zc = L.Nz;
-    double best = 1e300;
-    const int cmax = L.Nz / 4 > 1 ? L.Nz / 4 : 1;
-    for (int c = 1; c <= cmax; ++c) {
-        const int zc = (L.Nz + c - 1) / c;
-        const int ceff = (L.Nz + zc - 1) / zc;
-        const long long units = tiles * ceff;
-        const long long waves = (units + slots - 1) / slots;
-        const double cost = (double)waves * (zc + 8 * 0.35);
-        if (cost < best * 0.999) {
-            best = cost;
-            best_zc = zc;
-        }
-    }
-    a.zc = best_zc;
-    *grid = (int)(tiles * ((L.Nz + best_zc - 1) / best_zc));
-}
-
 int encode_map(CUtensorMap *map, const float *padded, const sgb_layout_info &L, int box_x, int box_y)
 {
     void *base = const_cast<float *>(padded) + L.origin;
@@ -258,13 +233,13 @@ int encode_map(CUtensorMap *map, const float *padded, const sgb_layout_info &L, 
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          SGB_L2PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return SGB_OK;
 }
 
 struct StepMaps {
-    CUtensorMap ucur, uprev, m, phi;
+    CUtensorMap ucur, ucur_in, uprev, m, phi;
 };
 
 int encode_step_maps(StepMaps &mp, const float *u_cur, const float *u_prev, const float *m,
@@ -272,6 +247,7 @@ int encode_step_maps(StepMaps &mp, const float *u_cur, const float *u_prev, cons
 {
     int rc;
     if ((rc = encode_map(&mp.ucur, u_cur, L, Cfg::SW, Cfg::SH))) return rc;
+    if ((rc = encode_map(&mp.ucur_in, u_cur, L, Cfg::BX, Cfg::BY))) return rc;
     if ((rc = encode_map(&mp.uprev, u_prev, L, Cfg::BX, Cfg::BY))) return rc;
     if ((rc = encode_map(&mp.m, m, L, Cfg::BX, Cfg::BY))) return rc;
     if ((rc = encode_map(&mp.phi, phi ? phi : u_prev, L, Cfg::BX, Cfg::BY))) return rc;
@@ -280,7 +256,7 @@ int encode_step_maps(StepMaps &mp, const float *u_cur, const float *u_prev, cons
 
 int launch_step(const StepArgs &a, const StepMaps &mp, int grid, cudaStream_t st)
 {
-    fused_step_kernel<Cfg><<<grid, Cfg::THREADS, Cfg::SMEM_BYTES, st>>>(a, mp.ucur, mp.uprev, mp.m,
+    fused_step_kernel<Cfg><<<grid, Cfg::BLOCK, Cfg::SMEM_BYTES, st>>>(a, mp.ucur, mp.ucur_in, mp.uprev, mp.m,
                                                                        mp.phi);
     CUDA_TRY(cudaGetLastError());
     ++t_launches;
@@ -467,7 +443,7 @@ extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_t
         a.wavelet = src->wavelet;
     }
     int grid = 0;
-    choose_decomposition(L, *ds, a, &grid);
+    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, ds->occ, a, &grid);
     StepMaps mp;
     if ((rc = encode_step_maps(mp, a.u_cur, a.u_out, m, phi, L))) return rc;
     if ((rc = launch_step(a, mp, grid, st))) return rc;
@@ -601,7 +577,7 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     base.rec_off = d_off;
     base.traces = d_tr;
     int grid = 0;
-    choose_decomposition(L, *ds, base, &grid);
+    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, ds->occ, base, &grid);
     StepMaps maps[2];  // [parity of n]
     for (int p = 0; p < 2; ++p)
         if ((rc = encode_step_maps(maps[p], buf[(p + 1) & 1], buf[p & 1], m, phi, L))) return rc;

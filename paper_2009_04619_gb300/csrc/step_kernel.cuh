@@ -17,17 +17,27 @@
 //  - one CTA owns a BX x BY tile of the x-y plane and streams a chunk of z
 //    (2.5D blocking);
 //  - planes of u^n arrive by TMA, with their radius-4 x-y halo, into an
-//    NU-stage shared-memory ring; u^{n-1}, m and (PML planes only) phi tiles
-//    into an NP-stage ring; one elected thread issues the copies, mbarriers
-//    carry completion, so several planes are always in flight;
+//    NU-stage shared-memory ring (the 4 planes below and above a z-chunk are
+//    only needed for the z-neighbours of the chunk's own points, so they come
+//    without the halo); u^{n-1}, m and (PML planes only) phi tiles
+//    into an NP-stage ring; one lane of a dedicated producer warp issues the
+//    copies in the order the consumers need them, as far ahead as the rings
+//    allow; "full" mbarriers carry copy completion to the consumer warps and
+//    "empty" mbarriers (one arrival per consumer warp) carry slot release back
+//    to the producer, so there is no block-wide barrier in the z loop;
 //  - each thread owns 4 consecutive x points (128-bit accesses) in TY rows;
-//    the z-neighbours of its points sit in a 9-deep register queue whose
-//    rotation is resolved at compile time by unrolling the z loop 9 times
-//    (the fixed-register idea of the paper's st_reg_fixed kernels);
+//    the z-neighbours of its points sit in a register queue (the paper's
+//    register-streaming idea, section IV); the z loop is unrolled U times with
+//    compile-time queue offsets and the queue shifts by U once per group, so
+//    there are 8 register moves per U planes.  Full 9-fold unrolling (the
+//    paper's st_reg_fixed form, no moves at all) measured slower on GB300:
+//    its code no longer fits the instruction cache;
 //  - whether a plane takes the PML path depends only on the tile and k, so
-//    the branch is uniform across the CTA; inside a PML-path plane, inner
-//    points select the Eq. 2 result computed by the same instructions as the
-//    inner path, bit for bit;
+//    the branch is uniform across the CTA: the z range of a tile splits into
+//    PML and interior segments, each a separately compiled loop, which keeps
+//    the hot interior loop small enough for the instruction cache; inside a
+//    PML-path plane, inner points select the Eq. 2 result computed by the same
+//    instructions as the interior path, bit for bit;
 //  - eta and its central differences are evaluated in closed form from the
 //    integer depth into the layer: no eta array is read;
 //  - every mbarrier wait is bounded (2 s); on timeout the CTA records
@@ -67,10 +77,13 @@ struct StepArgs {
     int tiles_x, tiles_y, zc;
 };
 
-template <int TXT_, int TYT_, int TY_, int NU_, int NP_, int MINB_>
+template <int TXT_, int TYT_, int TY_, int NU_, int NP_, int MINB_, int U_>
 struct TileCfg {
     static constexpr int TXT = TXT_, TYT = TYT_, TY = TY_, NU = NU_, NP = NP_, MINB = MINB_;
-    static constexpr int THREADS = TXT * TYT;
+    static constexpr int U = U_;       // z-loop unroll factor
+    static constexpr int QN = 8 + U_;  // register-queue length
+    static constexpr int THREADS = TXT * TYT;   // consumer (compute) threads
+    static constexpr int BLOCK = THREADS + 32;  // plus one producer warp
     static constexpr int BX = 4 * TXT, BY = TY * TYT;
     static constexpr int HX = 4;  // x margin of the u^n box: 16 bytes keeps TMA x aligned
     static constexpr int SW = BX + 2 * HX;
@@ -78,9 +91,12 @@ struct TileCfg {
     static constexpr int U_STAGE = SW * SH;
     static constexpr int P_TILE = BX * BY;
     static constexpr int P_STAGE = 3 * P_TILE;
+    static constexpr int WARPS = THREADS / 32;
     static constexpr size_t SMEM_BYTES =
-        size_t(NU * U_STAGE + NP * P_STAGE) * 4 + size_t(NU + NP) * 8 + size_t(NU + NP + 1) * 4;
+        size_t(NU * U_STAGE + NP * P_STAGE) * 4 + size_t(NU + NP) * 16 + size_t(NU + NP + 1) * 4;
     static_assert(NU >= 8, "the u ring must hold the 8 planes that prime the register queue");
+    static_assert(U_ >= 1 && U_ <= 9, "unroll factor");
+    static_assert(NP >= 2 && THREADS % 32 == 0, "ring sizes");
     static_assert((U_STAGE * 4) % 128 == 0 && (P_TILE * 4) % 128 == 0, "stage alignment");
     static_assert(SW <= 256 && SH <= 256 && BX <= 256 && BY <= 256, "TMA box limits");
 };
@@ -107,6 +123,7 @@ __device__ __forceinline__ void f4set(float4 &v, int e, float s)
     else if (e == 2) v.z = s;
     else v.w = s;
 }
+#ifdef SGB_SCALAR_FMA
 __device__ __forceinline__ void f4fma(float4 &acc, float c, const float4 &v)
 {
     acc.x = fmaf(c, v.x, acc.x);
@@ -114,31 +131,351 @@ __device__ __forceinline__ void f4fma(float4 &acc, float c, const float4 &v)
     acc.z = fmaf(c, v.z, acc.z);
     acc.w = fmaf(c, v.w, acc.w);
 }
+__device__ __forceinline__ float4 f4mul(float c, const float4 &v)
+{
+    return make_float4(c * v.x, c * v.y, c * v.z, c * v.w);
+}
+#else
+// acc += c * v on a float4 as two packed f32x2 FMAs.
+__device__ __forceinline__ void f4fma(float4 &acc, float c, const float4 &v)
+{
+    const float2 cc = make_float2(c, c);
+    float2 lo = __ffma2_rn(cc, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+    float2 hi = __ffma2_rn(cc, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
+    acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+__device__ __forceinline__ float4 f4mul(float c, const float4 &v)
+{
+    const float2 cc = make_float2(c, c);
+    float2 lo = __fmul2_rn(cc, make_float2(v.x, v.y));
+    float2 hi = __fmul2_rn(cc, make_float2(v.z, v.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+#endif
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+
+
+
+// Per-thread state of one fused-step work unit (a tile x a z-chunk).
+template <class C>
+struct StepCta {
+    static constexpr int TXT = C::TXT, TY = C::TY, NU = C::NU, NP = C::NP;
+    static constexpr int THREADS = C::THREADS, QN = C::QN, U = C::U, WARPS = C::WARPS;
+    static constexpr int BX = C::BX, BY = C::BY, HX = C::HX, SW = C::SW;
+    static constexpr int U_STAGE = C::U_STAGE, P_TILE = C::P_TILE, P_STAGE = C::P_STAGE;
+    static constexpr uint64_t WAIT_NS = 2000000000ull;
+
+    const StepArgs *pa;  // the kernel argument, in the constant parameter space
+    const CUtensorMap *tm_ucur, *tm_ucur_in, *tm_uprev, *tm_m, *tm_phi;
+    float *su, *sp;
+    uint64_t *full_u, *empty_u, *full_p, *empty_p;
+    int *lastf_u, *lastf_p, *s_abort;
+    long long base_off;  // element offset of (gi, gj0, k = 0)
+    int tid, lane, x0, y0, z0, z1, n, row0, colu, gi, gj0, prow;
+    bool xy_inner, aborted, store_ok;
+
+    __device__ __forceinline__ bool plane_pml(int k) const
+    {
+        return !xy_inner || k < pa->nb || k >= pa->nb + pa->nz;
+    }
+
+    __device__ __forceinline__ void wait(uint64_t *bar, uint32_t parity)
+    {
+        if (!mbar_wait_bounded(bar, parity, WAIT_NS)) {
+            *reinterpret_cast<volatile int *>(s_abort) = 1;
+            atomicOr(pa->err, DEV_ERR_TIMEOUT);
+        }
+    }
+
+    // Planes outside the chunk feed only the z-queue: no x-y halo needed.
+    __device__ __forceinline__ bool front_only(int p) const { return p < z0 || p >= z1; }
+
+    // Offset, inside a u stage holding plane p, of this thread's row-r float4.
+    __device__ __forceinline__ int own_off(int p, int r) const
+    {
+        return front_only(p) ? prow + r * BX : (row0 + r) * SW + colu;
+    }
+
+    __device__ __forceinline__ void issue_u(int p)
+    {
+        const int rel = p - z0 + 4;
+        const int s = rel % NU, f = rel / NU;
+        if (f > 0) wait(empty_u + s, (f - 1) & 1);  // previous plane of the slot released
+        lastf_u[s] = f;
+        if (front_only(p)) {
+            mbar_arrive_expect_tx(full_u + s, P_TILE * 4);
+            tma_load_3d(su + s * U_STAGE, tm_ucur_in, full_u + s, x0, y0, p);
+        } else {
+            mbar_arrive_expect_tx(full_u + s, U_STAGE * 4);
+            tma_load_3d(su + s * U_STAGE, tm_ucur, full_u + s, x0 - HX, y0 - R, p);
+        }
+    }
+
+    __device__ __forceinline__ void issue_p(int k)
+    {
+        const int rel = k - z0;
+        const int s = rel % NP, f = rel / NP;
+        if (f > 0) wait(empty_p + s, (f - 1) & 1);
+        lastf_p[s] = f;
+        const bool pml = plane_pml(k);
+        mbar_arrive_expect_tx(full_p + s, (pml ? 3 : 2) * P_TILE * 4);
+        float *d = sp + s * P_STAGE;
+#ifndef SGB_NO_HINT
+        const uint64_t pol = policy_evict_first();
+        tma_load_3d_hint(d, tm_uprev, full_p + s, x0, y0, k, pol);
+        tma_load_3d_hint(d + P_TILE, tm_m, full_p + s, x0, y0, k, pol);
+        if (pml) tma_load_3d_hint(d + 2 * P_TILE, tm_phi, full_p + s, x0, y0, k, pol);
+#else
+        tma_load_3d(d, tm_uprev, full_p + s, x0, y0, k);
+        tma_load_3d(d + P_TILE, tm_m, full_p + s, x0, y0, k);
+        if (pml) tma_load_3d(d + 2 * P_TILE, tm_phi, full_p + s, x0, y0, k);
+#endif
+    }
+
+    // Producer lane: every plane of u^n (z0-4 .. z1+3) and every (u^{n-1}, m,
+    // phi) plane (z0 .. z1-1), in the order the consumers need them; each
+    // refill first waits for its slot to be released.  Then waits for its own
+    // copies to land, so no copy is in flight when it exits.
+    __device__ __forceinline__ void produce()
+    {
+        int nu = z0 - 4, np = z0;
+        while ((nu < z1 + 4 || np < z1) && !aborted) {
+            // plane nu is first needed at iteration nu - z0 - 4 (as the front
+            // plane), plane np at iteration np - z0
+            const bool do_u = nu < z1 + 4 && (np >= z1 || nu - z0 - 4 <= np - z0);
+            if (do_u) issue_u(nu++);
+            else issue_p(np++);
+            aborted = *reinterpret_cast<volatile int *>(s_abort) != 0;
+        }
+        for (int s = 0; s < NU; ++s)
+            if (lastf_u[s] >= 0) mbar_wait_bounded(full_u + s, lastf_u[s] & 1, WAIT_NS);
+        for (int s = 0; s < NP; ++s)
+            if (lastf_p[s] >= 0) mbar_wait_bounded(full_p + s, lastf_p[s] & 1, WAIT_NS);
+    }
+
+    // One z-plane: iteration it (plane k = z0 + it).  The queue holds planes
+    // k-4 .. k+3 at q[O .. O+7]; the front plane k+4 is loaded into q[O+8].
+    template <int O, bool PML>
+    __device__ __forceinline__ void plane(float4 (&q)[TY][QN], int it)
+    {
+        const StepArgs &a = *pa;
+        const int k = z0 + it;
+        const int relf = it + 8;
+        const int sf = relf % NU;
+        wait(full_u + sf, (relf / NU) & 1);
+#pragma unroll
+        for (int r = 0; r < TY; ++r) q[r][O + 8] = lds128(su + sf * U_STAGE + own_off(k + 4, r));
+        const int sq = it % NP;
+        wait(full_p + sq, (it / NP) & 1);
+        const int sc = (it + 4) % NU;
+        const float *cu = su + sc * U_STAGE;
+        const float *pu = sp + sq * P_STAGE;
+
+        // 25-point Laplacian (Eq. 3): centre and z part from the queue
+        float4 L[TY], gy[TY];
+#pragma unroll
+        for (int r = 0; r < TY; ++r) {
+            L[r] = f4mul(a.c0, q[r][O + 4]);
+#pragma unroll
+            for (int m = 1; m <= R; ++m) {
+                f4fma(L[r], a.cz[m - 1], q[r][O + 4 - m]);
+                f4fma(L[r], a.cz[m - 1], q[r][O + 4 + m]);
+            }
+        }
+        // y part: rows -4 .. TY+3 around the thread's first row
+#pragma unroll
+        for (int d = -R; d < TY + R; ++d) {
+            float4 v;
+            if (d >= 0 && d < TY) v = q[d][O + 4];
+            else v = lds128(cu + (row0 + d) * SW + colu);
+#pragma unroll
+            for (int r = 0; r < TY; ++r) {
+                const int m = d > r ? d - r : r - d;
+                if (m >= 1 && m <= R) f4fma(L[r], a.cy[m - 1], v);
+                // gy = u(j+1) - u(j-1); row r-1 is visited before row r+1
+                if (PML && d == r - 1) gy[r] = make_float4(-v.x, -v.y, -v.z, -v.w);
+                if (PML && d == r + 1) f4fma(gy[r], 1.0f, v);
+            }
+        }
+        int dzk = 0;
+        float ez = 0.f, gzk = 0.f;
+        if (PML) {
+            dzk = pml_depth(a.nz, a.nb, k);
+            const int dzp = pml_depth(a.nz, a.nb, k + 1), dzm = pml_depth(a.nz, a.nb, k - 1);
+            ez = a.az * float(dzk * dzk);
+            gzk = a.kz * float(dzp * dzp - dzm * dzm);
+        }
+        const long long off0 = base_off + (long long)k * a.sxy;
+#pragma unroll
+        for (int r = 0; r < TY; ++r) {
+            const float *rowp = cu + (row0 + r) * SW + colu;
+            const float4 c = q[r][O + 4];
+            const float4 lf = lds128(rowp - 4), rt = lds128(rowp + 4);
+            const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w,
+                                 rt.x, rt.y, rt.z, rt.w};
+            float4 Lr = L[r];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float sacc = f4get(Lr, e);
+#pragma unroll
+                for (int m = 1; m <= R; ++m) {
+                    sacc = fmaf(a.cx[m - 1], w[4 + e - m], sacc);
+                    sacc = fmaf(a.cx[m - 1], w[4 + e + m], sacc);
+                }
+                f4set(Lr, e, sacc);
+            }
+            const int pr = prow + r * BX;
+            const float4 up = lds128(pu + pr);
+            const float4 mm = lds128(pu + P_TILE + pr);
+            float4 un;
+            un.x = interior_update(c.x, up.x, mm.x, Lr.x);
+            un.y = interior_update(c.y, up.y, mm.y, Lr.y);
+            un.z = interior_update(c.z, up.z, mm.z, Lr.z);
+            un.w = interior_update(c.w, up.w, mm.w, Lr.w);
+            const int j = gj0 + r;
+            float4 phn = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool any_pml = false;
+            if (PML) {
+                const float4 ph = lds128(pu + 2 * P_TILE + pr);
+                phn = ph;
+                const int dyj = pml_depth(a.ny, a.nb, j);
+                const int dyp = pml_depth(a.ny, a.nb, j + 1), dym = pml_depth(a.ny, a.nb, j - 1);
+                const float eyz = fmaf(a.ay, float(dyj * dyj), ez);
+                const float gyk = a.ky * float(dyp * dyp - dym * dym);
+                const float4 zp = q[r][O + 5], zm = q[r][O + 3];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = gi + e;
+                    const int dxi = pml_depth(a.nx, a.nb, i);
+                    const int dxp = pml_depth(a.nx, a.nb, i + 1), dxm = pml_depth(a.nx, a.nb, i - 1);
+                    const bool pt = (dxi | dyj | dzk) != 0;
+                    any_pml |= pt;
+                    const float edt = fmaf(a.ax, float(dxi * dxi), eyz);
+                    const float G = a.kx * float(dxp * dxp - dxm * dxm) * (w[5 + e] - w[3 + e]) +
+                                    gyk * f4get(gy[r], e) + gzk * (f4get(zp, e) - f4get(zm, e));
+                    const float inv = __frcp_rn(1.0f + edt);
+                    const float cc = f4get(c, e), pe = f4get(ph, e);
+                    const float upml = ((2.0f - edt * edt) * cc - (1.0f - edt) * f4get(up, e) +
+                                        f4get(mm, e) * (f4get(Lr, e) + pe)) * inv;
+                    const float ppml = (pe - G) * inv;
+                    if (pt) {
+                        f4set(un, e, upml);
+                        f4set(phn, e, ppml);
+                    }
+                }
+            }
+            // point source (Eq. 2 right-hand side), added by the owning thread
+            if (k == a.sk && j == a.sj && a.si >= gi && a.si < gi + 4) {
+                const int e = a.si - gi;
+                f4set(un, e, f4get(un, e) + f4get(mm, e) * a.wavelet[n] * a.inv_vol);
+            }
+            if (store_ok && j < a.Ny) {
+                const long long off = off0 + (long long)r * a.sx;
+                if (gi + 3 < a.Nx) {
+#ifdef SGB_STORE_EVICT_FIRST
+                    const uint64_t pol = policy_evict_first();
+                    stg128_hint(a.u_out + off, un, pol);
+                    if (PML && any_pml) stg128_hint(a.phi + off, phn, pol);
+#else
+                    stg128(a.u_out + off, un);
+                    if (PML && any_pml) stg128(a.phi + off, phn);
+#endif
+                } else {
+                    for (int e = 0; e < 4 && gi + e < a.Nx; ++e) {
+                        a.u_out[off + e] = f4get(un, e);
+                        if (PML && any_pml) a.phi[off + e] = f4get(phn, e);
+                    }
+                }
+            }
+        }
+        // release the current u plane and this p slot
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(empty_u + sc);
+            mbar_arrive(empty_p + sq);
+        }
+        aborted = *reinterpret_cast<volatile int *>(s_abort) != 0;
+    }
+
+    template <int O>
+    __device__ __forceinline__ void shift(float4 (&q)[TY][QN])
+    {
+#pragma unroll
+        for (int r = 0; r < TY; ++r)
+#pragma unroll
+            for (int jq = 0; jq < 8; ++jq) q[r][jq] = q[r][jq + O];
+    }
+
+    template <int O, bool PML>
+    __device__ __forceinline__ void group(float4 (&q)[TY][QN], int it)
+    {
+        if constexpr (O < U) {
+            plane<O, PML>(q, it + O);
+            group<O + 1, PML>(q, it);
+        }
+    }
+
+    // Iterations [it, it_end) of one kind (PML or interior): groups of U
+    // planes with compile-time queue offsets, then single planes.
+    template <bool PML>
+    __device__ __forceinline__ void segment(float4 (&q)[TY][QN], int it, int it_end)
+    {
+        if (U > 1) {
+            for (; it + U <= it_end && !aborted; it += U) {
+                group<0, PML>(q, it);
+                shift<U>(q);
+            }
+        }
+        for (; it < it_end && !aborted; ++it) {
+            plane<0, PML>(q, it);
+            shift<1>(q);
+        }
+    }
+};
 
 template <class C>
-__global__ void __launch_bounds__(C::THREADS, C::MINB)
-    fused_step_kernel(const StepArgs a, const __grid_constant__ CUtensorMap tm_ucur,
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+    fused_step_kernel(const __grid_constant__ StepArgs a,
+                      const __grid_constant__ CUtensorMap tm_ucur,
+                      const __grid_constant__ CUtensorMap tm_ucur_in,
                       const __grid_constant__ CUtensorMap tm_uprev,
                       const __grid_constant__ CUtensorMap tm_m,
                       const __grid_constant__ CUtensorMap tm_phi)
 {
-    constexpr int TXT = C::TXT, TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
-    constexpr int BX = C::BX, BY = C::BY, HX = C::HX, SW = C::SW;
-    constexpr int U_STAGE = C::U_STAGE, P_TILE = C::P_TILE, P_STAGE = C::P_STAGE;
-    constexpr uint64_t WAIT_NS = 2000000000ull;
+    using S = StepCta<C>;
+    constexpr int TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
+    constexpr int BX = C::BX, BY = C::BY;
+    constexpr int U_STAGE = C::U_STAGE, P_STAGE = C::P_STAGE;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *su = reinterpret_cast<float *>(smem_raw);
-    float *sp = su + NU * U_STAGE;
-    uint64_t *bar_u = reinterpret_cast<uint64_t *>(sp + NP * P_STAGE);
-    uint64_t *bar_p = bar_u + NU;
-    int *lastf_u = reinterpret_cast<int *>(bar_p + NP);
-    int *lastf_p = lastf_u + NU;
-    int &s_abort = lastf_p[NP];  // kept in the dynamic region: no static shared memory,
-                                 // so the TMA destinations start at the aligned base
+    S st;
+    st.pa = &a;
+    st.tm_ucur = &tm_ucur;
+    st.tm_ucur_in = &tm_ucur_in;
+    st.tm_uprev = &tm_uprev;
+    st.tm_m = &tm_m;
+    st.tm_phi = &tm_phi;
+    st.su = reinterpret_cast<float *>(smem_raw);
+    st.sp = st.su + NU * U_STAGE;
+    st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * P_STAGE);
+    st.empty_u = st.full_u + NU;
+    st.full_p = st.empty_u + NU;
+    st.empty_p = st.full_p + NP;
+    st.lastf_u = reinterpret_cast<int *>(st.empty_p + NP);
+    st.lastf_p = st.lastf_u + NU;
+    // kept in the dynamic region: no static shared memory, so the TMA
+    // destinations start at the aligned base
+    st.s_abort = st.lastf_p + NP;
 
     const int tid = threadIdx.x;
-    const int txi = tid % TXT, tyi = tid / TXT;
+    st.tid = tid;
+    st.lane = tid & 31;
 
     // Work unit: chunk-major so that CTAs running together share z and their
     // x-y halos meet in L2.
@@ -146,249 +483,82 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
     const int chunk = blockIdx.x / per_chunk;
     const int trem = blockIdx.x - chunk * per_chunk;
     const int tyl = trem / a.tiles_x, txl = trem - tyl * a.tiles_x;
-    const int x0 = txl * BX, y0 = tyl * BY;
-    const int z0 = chunk * a.zc;
-    const int z1 = min(z0 + a.zc, a.Nz);
-    const int nit = z1 - z0;
-    const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
+    st.x0 = txl * BX;
+    st.y0 = tyl * BY;
+    st.z0 = chunk * a.zc;
+    st.z1 = min(st.z0 + a.zc, a.Nz);
+    const int nit = st.z1 - st.z0;
+    st.n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
+    st.aborted = false;
 
     // Receivers of the previous step: u^n is read-only in this launch.
-    if (a.nrec > 0 && n >= 1) {
-        for (int r = blockIdx.x * THREADS + tid; r < a.nrec; r += gridDim.x * THREADS) {
+    if (a.nrec > 0 && st.n >= 1) {
+        for (int r = blockIdx.x * C::BLOCK + tid; r < a.nrec; r += gridDim.x * C::BLOCK) {
             const float v = a.u_cur[a.rec_off[r]];
-            a.traces[(long long)(n - 1) * a.nrec + r] = v;
+            a.traces[(long long)(st.n - 1) * a.nrec + r] = v;
             if (!isfinite(v)) atomicOr(a.err, DEV_ERR_NONFINITE);
         }
     }
 
-    const int xe = min(x0 + BX, a.Nx), ye = min(y0 + BY, a.Ny);
-    const bool xy_inner = x0 >= a.nb && xe <= a.nb + a.nx && y0 >= a.nb && ye <= a.nb + a.ny;
+    const int xe = min(st.x0 + BX, a.Nx), ye = min(st.y0 + BY, a.Ny);
+    st.xy_inner = st.x0 >= a.nb && xe <= a.nb + a.nx && st.y0 >= a.nb && ye <= a.nb + a.ny;
 
-    if (tid == 0) {
-        s_abort = 0;
+    if (tid == THREADS) {
+        *st.s_abort = 0;
         for (int i = 0; i < NU; ++i) {
-            mbar_init(bar_u + i, 1);
-            lastf_u[i] = -1;
+            mbar_init(st.full_u + i, 1);
+            mbar_init(st.empty_u + i, C::WARPS);
+            st.lastf_u[i] = -1;
         }
         for (int i = 0; i < NP; ++i) {
-            mbar_init(bar_p + i, 1);
-            lastf_p[i] = -1;
+            mbar_init(st.full_p + i, 1);
+            mbar_init(st.empty_p + i, C::WARPS);
+            st.lastf_p[i] = -1;
         }
         fence_barrier_init();
     }
     __syncthreads();
     if (nit <= 0) return;
 
-    auto plane_pml = [&](int k) { return !xy_inner || k < a.nb || k >= a.nb + a.nz; };
-    auto issue_u = [&](int p) {
-        const int rel = p - z0 + 4;
-        const int s = rel % NU;
-        lastf_u[s] = rel / NU;
-        mbar_arrive_expect_tx(bar_u + s, U_STAGE * 4);
-        tma_load_3d(su + s * U_STAGE, &tm_ucur, bar_u + s, x0 - HX, y0 - R, p);
-    };
-    auto issue_p = [&](int k) {
-        const int rel = k - z0;
-        const int s = rel % NP;
-        lastf_p[s] = rel / NP;
-        const bool pml = plane_pml(k);
-        const uint64_t pol = policy_evict_first();
-        mbar_arrive_expect_tx(bar_p + s, (pml ? 3 : 2) * P_TILE * 4);
-        float *d = sp + s * P_STAGE;
-        tma_load_3d_hint(d, &tm_uprev, bar_p + s, x0, y0, k, pol);
-        tma_load_3d_hint(d + P_TILE, &tm_m, bar_p + s, x0, y0, k, pol);
-        if (pml) tma_load_3d_hint(d + 2 * P_TILE, &tm_phi, bar_p + s, x0, y0, k, pol);
-    };
-
-    if (tid == 0) {
-        for (int p = z0 - 4; p < z0 - 4 + NU && p < z1 + 4; ++p) issue_u(p);
-        for (int k = z0; k < z0 + NP && k < z1; ++k) issue_p(k);
+    if (tid >= THREADS) {  // producer warp: one lane issues every copy
+        if (tid == THREADS) st.produce();
+        return;
     }
 
-    const int row0 = R + TY * tyi;  // first own row inside a u stage
-    const int colu = HX + 4 * txi;  // own column inside a u stage
-    const int gi = x0 + 4 * txi;    // first own x
-    const int gj0 = y0 + TY * tyi;  // first own y
+    const int txi = tid % C::TXT, tyi = tid / C::TXT;
+    st.row0 = R + TY * tyi;
+    st.colu = C::HX + 4 * txi;
+    st.gi = st.x0 + 4 * txi;
+    st.gj0 = st.y0 + TY * tyi;
+    st.prow = (TY * tyi) * BX + 4 * txi;
+    st.store_ok = st.gi < a.Nx;
+    st.base_off = a.origin + (long long)st.gj0 * a.sx + st.gi;
 
-    // Prime the register queue with planes z0-4 .. z0+3.
-    float4 q[TY][9];
-    bool ok = true;
+    // Prime the register queue with planes z0-4 .. z0+3 (first fill of slots 0..7).
+    float4 q[TY][C::QN];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-        ok &= mbar_wait_bounded(bar_u + s, 0, WAIT_NS);
+        st.wait(st.full_u + s, 0);
 #pragma unroll
-        for (int r = 0; r < TY; ++r) q[r][s] = lds128(su + s * U_STAGE + (row0 + r) * SW + colu);
+        for (int r = 0; r < TY; ++r)
+            q[r][s] = lds128(st.su + s * U_STAGE + st.own_off(st.z0 - 4 + s, r));
     }
-    if (!ok) {
-        s_abort = 1;
-        atomicOr(a.err, DEV_ERR_TIMEOUT);
-    }
-    __syncthreads();
-    if (tid == 0 && !s_abort)
-        for (int p = z0 - 4; p < z0; ++p)
-            if (p + NU < z1 + 4) issue_u(p + NU);
+    // planes z0-4 .. z0-1 (slots 0..3) are not needed again
+    __syncwarp();
+    if (st.lane == 0)
+        for (int s = 0; s < 4; ++s) mbar_arrive(st.empty_u + s);
+    st.aborted = *reinterpret_cast<volatile int *>(st.s_abort) != 0;
 
-    bool aborted = s_abort != 0;
-    for (int it0 = 0; it0 < nit && !aborted; it0 += 9) {
-#pragma unroll
-        for (int rr = 0; rr < 9; ++rr) {
-            const int it = it0 + rr;
-            if (it >= nit) break;
-            const int k = z0 + it;
-            // Front plane k + 4 enters the queue.
-            {
-                const int rel = it + 8;
-                const int s = rel % NU;
-                if (!mbar_wait_bounded(bar_u + s, (rel / NU) & 1, WAIT_NS)) {
-                    s_abort = 1;
-                    atomicOr(a.err, DEV_ERR_TIMEOUT);
-                }
-#pragma unroll
-                for (int r = 0; r < TY; ++r)
-                    q[r][(rr + 8) % 9] = lds128(su + s * U_STAGE + (row0 + r) * SW + colu);
-            }
-            const int sq = it % NP;
-            if (!mbar_wait_bounded(bar_p + sq, (it / NP) & 1, WAIT_NS)) {
-                s_abort = 1;
-                atomicOr(a.err, DEV_ERR_TIMEOUT);
-            }
-            const float *cu = su + ((it + 4) % NU) * U_STAGE;
-            const float *pu = sp + sq * P_STAGE;
-            const bool pml = plane_pml(k);
-
-            // 25-point Laplacian (Eq. 3) of the TY x 4 own points.
-            float4 L[TY], gy[TY];
-#pragma unroll
-            for (int r = 0; r < TY; ++r) {
-                const float4 c = q[r][(rr + 4) % 9];
-                L[r] = make_float4(a.c0 * c.x, a.c0 * c.y, a.c0 * c.z, a.c0 * c.w);
-                gy[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int m = 1; m <= R; ++m) {
-                    f4fma(L[r], a.cz[m - 1], q[r][(rr + 4 - m + 9) % 9]);
-                    f4fma(L[r], a.cz[m - 1], q[r][(rr + 4 + m) % 9]);
-                }
-            }
-            // y neighbours: rows -4 .. TY+3 relative to the first own row.
-#pragma unroll
-            for (int d = -R; d < TY + R; ++d) {
-                float4 v;
-                if (d >= 0 && d < TY) v = q[d][(rr + 4) % 9];
-                else v = lds128(cu + (row0 + d) * SW + colu);
-#pragma unroll
-                for (int r = 0; r < TY; ++r) {
-                    const int m = d > r ? d - r : r - d;
-                    if (m >= 1 && m <= R) f4fma(L[r], a.cy[m - 1], v);
-                    if (d == r + 1) {
-                        gy[r].x += v.x;
-                        gy[r].y += v.y;
-                        gy[r].z += v.z;
-                        gy[r].w += v.w;
-                    }
-                    if (d == r - 1) {
-                        gy[r].x -= v.x;
-                        gy[r].y -= v.y;
-                        gy[r].z -= v.z;
-                        gy[r].w -= v.w;
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < TY; ++r) {
-                const float *rowp = cu + (row0 + r) * SW + colu;
-                const float4 c = q[r][(rr + 4) % 9];
-                const float4 lf = lds128(rowp - 4), rt = lds128(rowp + 4);
-                const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w,
-                                     rt.x, rt.y, rt.z, rt.w};
-                float4 Lr = L[r];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float s = f4get(Lr, e);
-#pragma unroll
-                    for (int m = 1; m <= R; ++m) {
-                        s = fmaf(a.cx[m - 1], w[4 + e - m], s);
-                        s = fmaf(a.cx[m - 1], w[4 + e + m], s);
-                    }
-                    f4set(Lr, e, s);
-                }
-                const int prow = (TY * tyi + r) * BX + 4 * txi;
-                const float4 up = lds128(pu + prow);
-                const float4 mm = lds128(pu + P_TILE + prow);
-                float4 un;
-                un.x = interior_update(c.x, up.x, mm.x, Lr.x);
-                un.y = interior_update(c.y, up.y, mm.y, Lr.y);
-                un.z = interior_update(c.z, up.z, mm.z, Lr.z);
-                un.w = interior_update(c.w, up.w, mm.w, Lr.w);
-                const int j = gj0 + r;
-                float4 phn;
-                bool any_pml = false;
-                if (pml) {
-                    const float4 ph = lds128(pu + 2 * P_TILE + prow);
-                    phn = ph;
-                    const int dyj = pml_depth(a.ny, a.nb, j);
-                    const int dyp = pml_depth(a.ny, a.nb, j + 1), dym = pml_depth(a.ny, a.nb, j - 1);
-                    const int dzk = pml_depth(a.nz, a.nb, k);
-                    const int dzp = pml_depth(a.nz, a.nb, k + 1), dzm = pml_depth(a.nz, a.nb, k - 1);
-                    const float ey = a.ay * float(dyj * dyj) + a.az * float(dzk * dzk);
-                    const float gyc = a.ky * float(dyp * dyp - dym * dym);
-                    const float gzc = a.kz * float(dzp * dzp - dzm * dzm);
-                    const float4 zp = q[r][(rr + 5) % 9], zm = q[r][(rr + 3) % 9];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int i = gi + e;
-                        const int dxi = pml_depth(a.nx, a.nb, i);
-                        const int dxp = pml_depth(a.nx, a.nb, i + 1), dxm = pml_depth(a.nx, a.nb, i - 1);
-                        const bool pt = (dxi | dyj | dzk) != 0;
-                        any_pml |= pt;
-                        const float edt = fmaf(a.ax, float(dxi * dxi), ey);
-                        const float G = a.kx * float(dxp * dxp - dxm * dxm) * (w[5 + e] - w[3 + e]) +
-                                        gyc * f4get(gy[r], e) +
-                                        gzc * (f4get(zp, e) - f4get(zm, e));
-                        const float inv = 1.0f / (1.0f + edt);
-                        const float cc = f4get(c, e), pe = f4get(ph, e);
-                        const float upml =
-                            ((2.0f - edt * edt) * cc - (1.0f - edt) * f4get(up, e) +
-                             f4get(mm, e) * (f4get(Lr, e) + pe)) * inv;
-                        const float ppml = (pe - G) * inv;
-                        if (pt) {
-                            f4set(un, e, upml);
-                            f4set(phn, e, ppml);
-                        }
-                    }
-                }
-                // Point source (Eq. 2 right-hand side), added by the owning thread.
-                if (k == a.sk && j == a.sj && a.si >= gi && a.si < gi + 4) {
-                    const int e = a.si - gi;
-                    f4set(un, e, f4get(un, e) + f4get(mm, e) * a.wavelet[n] * a.inv_vol);
-                }
-                if (j < a.Ny && gi < a.Nx) {
-                    const long long off = a.origin + (long long)k * a.sxy + (long long)j * a.sx + gi;
-                    if (gi + 3 < a.Nx) {
-                        stg128(a.u_out + off, un);
-                        if (any_pml) stg128(a.phi + off, phn);
-                    } else {
-                        for (int e = 0; e < 4 && gi + e < a.Nx; ++e) {
-                            a.u_out[off + e] = f4get(un, e);
-                            if (any_pml) a.phi[off + e] = f4get(phn, e);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            aborted = s_abort != 0;
-            if (aborted) break;
-            if (tid == 0) {
-                if (k + NU < z1 + 4) issue_u(k + NU);
-                if (k + NP < z1) issue_p(k + NP);
-            }
-        }
-    }
-    if (aborted && tid == 0) {
-        // Drain this CTA's own copies still in flight (bounded) before exiting.
-        for (int s = 0; s < NU; ++s)
-            if (lastf_u[s] >= 0) mbar_wait_bounded(bar_u + s, lastf_u[s] & 1, WAIT_NS);
-        for (int s = 0; s < NP; ++s)
-            if (lastf_p[s] >= 0) mbar_wait_bounded(bar_p + s, lastf_p[s] & 1, WAIT_NS);
+    // z segments: PML planes below the inner region, interior planes, PML
+    // planes above it (all PML for tiles touching the x-y PML band).
+    if (!st.xy_inner) {
+        st.template segment<true>(q, 0, nit);
+    } else {
+        const int a0 = min(max(a.nb - st.z0, 0), nit);
+        const int a1 = min(max(a.nb + a.nz - st.z0, a0), nit);
+        st.template segment<true>(q, 0, a0);
+        st.template segment<false>(q, a0, a1);
+        st.template segment<true>(q, a1, nit);
     }
 }
 

@@ -1,0 +1,58 @@
+"""Launch the fused step kernel back to back on a synthetic grid and report its
+time per launch (CUDA events) -- a small driver for timing and for ncu captures.
+
+    python -m paper_2009_04619_gb300.profile_step --n 256 --nb 32 --launches 20
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import build, seisgb
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--n", type=int, default=256, help="computed points per axis")
+    p.add_argument("--nb", type=int, default=32)
+    p.add_argument("--launches", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--lib", default=None, help="path of an alternative libseisgb.so build")
+    a = p.parse_args(argv)
+    if a.lib:
+        seisgb.LIB_PATH = a.lib
+    else:
+        build.build()
+    n_in = a.n - 2 * a.nb  # nb = 0: no PML, every tile takes the interior path
+    h, v = 10.0, 4500.0
+    g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, h, h, h, 1.0, v)
+    dt = 0.4 * seisgb.cfl_dt(g0, v)
+    g = seisgb.make_grid(n_in, n_in, n_in, a.nb, h, h, h, dt, v)
+    L = seisgb.layout(g)
+    f = [torch.zeros(int(L.elems), dtype=torch.float32, device="cuda") for _ in range(4)]
+    vel = torch.full(g.shape, 3000.0, device="cuda")
+    seisgb.pack(g, (vel * dt) ** 2, f[2])
+    w = torch.zeros(a.warmup + a.launches + 1, device="cuda")
+    src = (a.n // 2, a.n // 2, a.n // 2)
+    for n in range(a.warmup):
+        seisgb.stencil_step(g, f[n % 2], f[(n + 1) % 2], f[2], f[3], n, source=(*src, w))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for n in range(a.launches):
+        seisgb.stencil_step(g, f[n % 2], f[(n + 1) % 2], f[2], f[3], n, source=(*src, w))
+    e1.record()
+    torch.cuda.synchronize()
+    seisgb.device_status()
+    ms = e0.elapsed_time(e1) / a.launches
+    pts = a.n ** 3
+    alg = 16 * pts + 8 * (pts - n_in ** 3)
+    print(json.dumps({"n": a.n, "nb": a.nb, "ms_per_launch": ms, "gpts": pts / ms / 1e6,
+                      "alg_gbs": alg / ms / 1e6, "lib": a.lib or seisgb.LIB_PATH}))
+
+
+if __name__ == "__main__":
+    main()
