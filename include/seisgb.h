@@ -124,6 +124,29 @@ int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int
              const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
              float *final_u, void *stream);
 
+/* Allocation-free variant of run_shot (the paper has no counterpart).  For
+ * callers that cannot allocate device memory once running -- e.g. a serving
+ * process whose device memory is all held by another allocator's pool, or a
+ * real-time loop that forbids cudaMalloc/cudaFree after start-up.  Same
+ * arguments, results and kernels as run_shot, except:
+ *  - velocity, wavelet, traces and final_u must be DEVICE pointers (rec_ijk and
+ *    src_ijk stay host arrays); nothing is allocated: all scratch (two
+ *    wavefields, phi, m, receiver tables) lives in one fixed 32 MiB device
+ *    array inside this library, which every GPU that loads the library holds
+ *    until the process exits;
+ *  - grids whose scratch does not fit (about 2 M padded points per field, e.g.
+ *    up to ~120^3 computed points) are rejected with SGB_ERR_INVALID_ARG and a
+ *    message naming the size;
+ *  - the first call on a device resolves the array's device address (set-up);
+ *    make that first call before any stream capture;
+ *  - all calls share the array and it keeps the previous call's contents (each
+ *    call clears what must start at zero); calls whose GPU work overlaps, on
+ *    any streams, race on it and give wrong results;
+ *  - the time loop is launched directly, one kernel per step (no CUDA graph). */
+int run_shot_noalloc(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
+                     const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
+                     float *final_u, void *stream);
+
 /* Layout conversion between compact (Nz, Ny, Nx) fp32 arrays and the padded
  * layout (device pointers; pack zeroes the halo).  Asynchronous on stream. */
 int sgb_pack(const sgb_grid *g, const float *compact, float *padded, void *stream);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -649,6 +650,209 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     }
     int dev_err = 0;
     if ((rc = read_and_clear_dev_err(*ds, st, &dev_err))) return rc;
+    if (dev_err & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a step kernel wait timed out");
+    if (dev_err & DEV_ERR_NONFINITE) return fail(SGB_ERR_NONFINITE, "a receiver sampled NaN/Inf");
+    return SGB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free shot.  Some callers cannot allocate device memory once they
+// are running: a serving process whose device memory is all held by another
+// allocator's pool, or a real-time loop that forbids cudaMalloc/cudaFree (and
+// the device-wide synchronisation they can imply) after start-up.  For them,
+// run_shot_noalloc takes its scratch from a fixed file-scope device array
+// instead of the library's pool.
+// ---------------------------------------------------------------------------
+#define SGB_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+// Scratch of run_shot_noalloc: two wavefields, phi, m, receiver tables.  Every
+// GPU that loads this library holds it until the process exits.  In host code
+// this name is only a stand-in: kernels get the device address obtained with
+// cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SGB_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+struct NoAllocState {
+    bool ready = false;
+    unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch
+    int *err = nullptr;                // device address of g_dev_err
+    int sms = 0, occ = 0;
+};
+NoAllocState g_noalloc[64];
+
+// Once per device, with that device current: resolve the device addresses of
+// the scratch array and the error word, and the step kernel's launch limits.
+int noalloc_setup(NoAllocState **out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SGB_ERR_CUDA, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    NoAllocState &s = g_noalloc[dev];
+    if (!s.ready) {
+        CUDA_TRY(cudaGetSymbolAddress((void **)&s.scratch, g_noalloc_scratch));
+        CUDA_TRY(cudaGetSymbolAddress((void **)&s.err, g_dev_err));
+        CUDA_TRY(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev));
+        CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel<Cfg>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)Cfg::SMEM_BYTES));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.occ, fused_step_kernel<Cfg>,
+                                                               Cfg::BLOCK, Cfg::SMEM_BYTES));
+        if (s.occ < 1) return fail(SGB_ERR_CUDA, "step kernel does not fit on an SM");
+        if (!g_encode) {
+            cudaDriverEntryPointQueryResult q;
+            void *fn = nullptr;
+            CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                      cudaEnableDefault, &q));
+            if (q != cudaDriverEntryPointSuccess || !fn)
+                return fail(SGB_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+        s.ready = true;
+    }
+    *out = &s;
+    return SGB_OK;
+}
+
+__global__ void rec_offsets_kernel(const int32_t *ijk, int nrec, long long sx, long long sxy,
+                                   long long origin, long long *off)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nrec)
+        off[r] = origin + (long long)ijk[3 * r + 2] * sxy + (long long)ijk[3 * r + 1] * sx +
+                 ijk[3 * r];
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const float *wavelet,
+                                int32_t nt, const int32_t *src_ijk, const int32_t *rec_ijk,
+                                int32_t nrec, float *traces, float *final_u, void *stream)
+{
+    sgb_layout_info L;
+    int rc = check_grid(g, &L);
+    if (rc) return rc;
+    if (g->storage != SGB_FP32)
+        return fail(SGB_ERR_INVALID_ARG, "run_shot_noalloc: only SGB_FP32 storage");
+    if (!velocity) return fail(SGB_ERR_INVALID_ARG, "velocity is NULL");
+    if (nt < 0) return fail(SGB_ERR_INVALID_ARG, "nt must be >= 0");
+    if (nt > 0 && src_ijk && !wavelet) return fail(SGB_ERR_INVALID_ARG, "wavelet is NULL");
+    if (nrec < 0) return fail(SGB_ERR_INVALID_ARG, "nrec < 0");
+    if (nrec > 0 && (!rec_ijk || !traces)) return fail(SGB_ERR_INVALID_ARG, "receiver arrays NULL");
+    if (src_ijk && !in_inner(g, src_ijk[0], src_ijk[1], src_ijk[2]))
+        return fail(SGB_ERR_INVALID_ARG, "source (%d,%d,%d) outside the inner region", src_ijk[0],
+                    src_ijk[1], src_ijk[2]);
+    for (int r = 0; r < nrec; ++r)
+        if (!in_inner(g, rec_ijk[3 * r], rec_ijk[3 * r + 1], rec_ijk[3 * r + 2]))
+            return fail(SGB_ERR_INVALID_ARG, "receiver %d outside the inner region", r);
+    // scratch layout inside the fixed array
+    const size_t fbytes = align256((size_t)L.elems * 4);
+    const size_t off_u0 = 0, off_u1 = fbytes, off_phi = 2 * fbytes, off_m = 3 * fbytes;
+    const size_t off_ijk = 4 * fbytes;
+    const size_t off_rec = off_ijk + align256((size_t)nrec * 12);
+    const size_t off_range = off_rec + align256((size_t)nrec * 8);
+    const size_t need = off_range + 256;
+    if (need > SGB_NOALLOC_SCRATCH_BYTES)
+        return fail(SGB_ERR_INVALID_ARG,
+                    "run_shot_noalloc: this grid and receiver set need %zu bytes of scratch, above "
+                    "the fixed %u bytes (about 2M padded points per field); use run_shot",
+                    need, (unsigned)SGB_NOALLOC_SCRATCH_BYTES);
+    const bool dev_ok = is_device_ptr(velocity) && (!src_ijk || nt == 0 || is_device_ptr(wavelet)) &&
+                        (nrec == 0 || is_device_ptr(traces)) && (!final_u || is_device_ptr(final_u));
+    if (!dev_ok)
+        return fail(SGB_ERR_INVALID_ARG,
+                    "run_shot_noalloc: velocity, wavelet, traces and final_u must be device pointers");
+    NoAllocState *ns;
+    if ((rc = noalloc_setup(&ns))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *base = ns->scratch;
+    float *u0 = (float *)(base + off_u0), *u1 = (float *)(base + off_u1);
+    float *phi = (float *)(base + off_phi), *m = (float *)(base + off_m);
+    int32_t *d_ijk = (int32_t *)(base + off_ijk);
+    long long *d_off = (long long *)(base + off_rec);
+    int *d_range = (int *)(base + off_range);
+    const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
+    const int ewg = (int)std::min<long long>((ncomp + 255) / 256, (long long)ns->sms * 8);
+
+    // the array keeps the previous call's contents: clear what must start at zero
+    int zero = 0, dev_err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&dev_err, ns->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaMemcpyAsync(ns->err, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(base, 0, off_ijk, st));  // u0, u1, phi, m
+    int init[4] = {0, 0x7f7fffff, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(d_range, init, sizeof init, cudaMemcpyHostToDevice, st));
+    vel_range_kernel<<<ewg, 256, 0, st>>>(velocity, ncomp, d_range);
+    CUDA_TRY(cudaGetLastError());
+    ++t_launches;
+    int range[4];
+    CUDA_TRY(cudaMemcpyAsync(range, d_range, sizeof range, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (range[2] != 0) return fail(SGB_ERR_INVALID_ARG, "velocity has non-positive or non-finite values");
+    float vmax_model;
+    memcpy(&vmax_model, &range[0], 4);
+    if ((double)g->dt > cfl_limit(g, vmax_model))
+        return fail(SGB_ERR_UNSTABLE_DT, "dt %g above the CFL limit %g of the model (vmax %g)",
+                    (double)g->dt, cfl_limit(g, vmax_model), (double)vmax_model);
+    make_m_kernel<<<ewg, 256, 0, st>>>(pad_geom(L), velocity, g->dt, m);
+    CUDA_TRY(cudaGetLastError());
+    ++t_launches;
+    if (nrec > 0) {
+        CUDA_TRY(cudaMemcpyAsync(d_ijk, rec_ijk, (size_t)nrec * 12, cudaMemcpyHostToDevice, st));
+        rec_offsets_kernel<<<(nrec + 255) / 256, 256, 0, st>>>(d_ijk, nrec, L.sx, L.stride_z,
+                                                               L.origin, d_off);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+    }
+
+    float *buf[2] = {u0, u1};  // buf[0] = u^{-1}, buf[1] = u^0
+    StepArgs base_args;
+    fill_step_constants(g, L, base_args);
+    base_args.phi = phi;
+    base_args.err = ns->err;
+    if (src_ijk) {
+        base_args.si = src_ijk[0];
+        base_args.sj = src_ijk[1];
+        base_args.sk = src_ijk[2];
+        base_args.wavelet = wavelet;
+    }
+    base_args.nrec = nrec;
+    base_args.rec_off = d_off;
+    base_args.traces = traces;
+    int grid = 0;
+    choose_decomposition(L.Nx, L.Ny, L.Nz, ns->sms, ns->occ, base_args, &grid);
+    StepMaps maps[2];
+    for (int p = 0; p < 2; ++p)
+        if ((rc = encode_step_maps(maps[p], buf[(p + 1) & 1], buf[p & 1], m, phi, L))) return rc;
+    for (int n = 0; n < nt; ++n) {
+        StepArgs a = base_args;
+        a.u_out = buf[n & 1];
+        a.u_cur = buf[(n + 1) & 1];
+        a.step_ptr = nullptr;
+        a.step_add = n;
+        if ((rc = launch_step(a, maps[n & 1], grid, st))) return rc;
+    }
+    float *u_last = nt > 0 ? buf[(nt - 1) & 1] : buf[1];
+    if (nrec > 0 && nt > 0) {
+        gather_kernel<<<(nrec + 255) / 256, 256, 0, st>>>(u_last, d_off, nrec,
+                                                          traces + (size_t)(nt - 1) * nrec, ns->err);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+    }
+    if (final_u) {
+        unpack_kernel<<<ewg, 256, 0, st>>>(pad_geom(L), u_last, final_u);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+    }
+    CUDA_TRY(cudaMemcpyAsync(&dev_err, ns->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (dev_err) {
+        CUDA_TRY(cudaMemcpyAsync(ns->err, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
     if (dev_err & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a step kernel wait timed out");
     if (dev_err & DEV_ERR_NONFINITE) return fail(SGB_ERR_NONFINITE, "a receiver sampled NaN/Inf");
     return SGB_OK;

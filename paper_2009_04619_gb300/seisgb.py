@@ -82,6 +82,10 @@ SIGNATURES = {
     "run_shot": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "run_shot_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "sgb_pack": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p]),
     "sgb_unpack": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
@@ -183,6 +187,22 @@ def run_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, traces, fina
                           None if s is None else s.ctypes.data,
                           r.ctypes.data if nrec else None, nrec,
                           _ptr(traces) if nrec else None, _ptr(final_u), _stream(stream)))
+
+
+def run_shot_noalloc(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, traces,
+                     final_u=None, stream=None):
+    """run_shot for callers that cannot allocate device memory: same arguments
+    (device tensors only for velocity / wavelet / traces / final_u); scratch comes
+    from a fixed device array inside the library (small grids only, see the C
+    header).  Calls must not overlap on the GPU."""
+    s = None if src_ijk is None else np.ascontiguousarray(np.asarray(src_ijk, dtype=np.int32))
+    r = np.ascontiguousarray(np.asarray(rec_ijk, dtype=np.int32).reshape(-1, 3))
+    nrec = r.shape[0]
+    _check(lib().run_shot_noalloc(ctypes.byref(g), _ptr(velocity), _ptr(wavelet), int(nt),
+                                  None if s is None else s.ctypes.data,
+                                  r.ctypes.data if nrec else None, nrec,
+                                  _ptr(traces) if nrec else None, _ptr(final_u),
+                                  _stream(stream)))
 
 
 def pack(g: Grid, compact, padded, stream=None):
