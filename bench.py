@@ -87,12 +87,13 @@ def _peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def _alg_bytes_per_launch(w):
+def _alg_bytes_per_launch(w, wave_bytes=4):
     """Compulsory bytes of one step: read u^n, u^{n-1}, m and write u^{n+1}
-    (16 B per point, fp32) plus phi read + write (8 B) at PML points."""
+    (3 x wave_bytes + 4 B of m per point: 16 B in fp32, 10 B with 16-bit
+    wavefields) plus the fp32 phi read + write (8 B) at PML points."""
     N = w.points
     inner = w.nx * w.ny * w.nz
-    return 16 * N + 8 * (N - inner)
+    return (3 * wave_bytes + 4) * N + 8 * (N - inner)
 
 
 class ClockSampler:
@@ -284,6 +285,27 @@ def main():
     traffic = NCU_TRAFFIC.get(_kernel_hash())
     del bufs, d_m
 
+    # the same shot with 16-bit wavefield storage (fp32 arithmetic)
+    precision = {}
+    for fname, fmt in (("fp16_scaled", seisgb.FP16_SCALED), ("bf16", seisgb.BF16)):
+        gp = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, storage=fmt)
+        seisgb.run_shot(gp, d_v, d_w, w.nt, src, rec, d_tr)
+        barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(a.steps):
+            seisgb.run_shot(gp, d_v, d_w, w.nt, src, rec, d_tr)
+        p1.record(stream)
+        barrier()
+        pms = p0.elapsed_time(p1) / a.steps
+        alg16 = _alg_bytes_per_launch(w, wave_bytes=2)
+        precision[fname] = {
+            "value": w.points * w.nt * world / (pms / 1e3) / 1e9, "unit": UNIT,
+            "ms_per_step": pms, "alg_bytes_per_launch": alg16,
+            "achieved_gbs": alg16 / (pms / w.nt / 1e3) / 1e9,
+            "frac": alg16 / (pms / w.nt / 1e3) / 1e9 / peak,
+            "error": "relative L2 vs the fp64 oracle: see the 256^3 x 1000-step precision test"}
+
     # end to end through the C ABI with pinned host buffers: velocity and wavelet
     # copied in, traces copied out, every step
     h_v = torch.from_numpy(vel).pin_memory()
@@ -322,6 +344,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
+        "precision": precision,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle

@@ -2,6 +2,8 @@
 // velocity range, receiver gathers and the graph step counter.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace sgb {
 
@@ -88,6 +90,33 @@ __global__ void gather_kernel(const float *__restrict__ u, const long long *__re
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < nrec) {
         const float v = u[off[r]];
+        row[r] = v;
+        if (!isfinite(v)) atomicOr(err, 2);
+    }
+}
+
+// 16-bit (or fp32) field -> fp32 compact, times the field's scale (null: 1).
+template <class T>
+__global__ void unpack_t_kernel(PadGeom g, const T *__restrict__ src, const float *scale,
+                                float *__restrict__ dst)
+{
+    const float s = scale ? *scale : 1.0f;
+    const long long n = (long long)g.Nx * g.Ny * g.Nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+        const long long i = c % g.Nx, t = c / g.Nx;
+        const long long j = t % g.Ny, k = t / g.Ny;
+        dst[c] = (float)src[g.origin + k * g.sxy + j * g.sx + i] * s;
+    }
+}
+
+template <class T>
+__global__ void gather_t_kernel(const T *__restrict__ u, const long long *__restrict__ off, int nrec,
+                                const float *scale, float *__restrict__ row, int *err)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nrec) {
+        const float v = (float)u[off[r]] * (scale ? *scale : 1.0f);
         row[r] = v;
         if (!isfinite(v)) atomicOr(err, 2);
     }

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/seisgb.h"
@@ -69,7 +70,9 @@ namespace {
 struct DevState {
     bool ready = false;
     int sms = 0;
-    int occ = 0;  // resident CTAs of the step kernel per SM
+    int occ = 0;     // resident CTAs of the fp32 step kernel per SM
+    int occ_h = 0;   // ... fp16 storage
+    int occ_b = 0;   // ... bf16 storage
     int *err = nullptr;
     cudaMemPool_t pool = nullptr;
 };
@@ -77,6 +80,21 @@ struct DevState {
 std::mutex g_mu;
 DevState g_dev[64];
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+// Allow the step kernel for storage T its dynamic shared memory; report how
+// many of its CTAs fit on one SM.
+template <class T>
+int prepare_step_kernel(int *occ)
+{
+    using G = Stage<Cfg, T>;
+    CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel<Cfg, T>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)G::SMEM_BYTES));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fused_step_kernel<Cfg, T>,
+                                                           Cfg::BLOCK, G::SMEM_BYTES));
+    if (*occ < 1) return fail(SGB_ERR_CUDA, "step kernel does not fit on an SM");
+    return SGB_OK;
+}
 
 int device_state(DevState **out)
 {
@@ -87,12 +105,10 @@ int device_state(DevState **out)
     DevState &s = g_dev[dev];
     if (!s.ready) {
         CUDA_TRY(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev));
-        CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel<Cfg>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)Cfg::SMEM_BYTES));
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.occ, fused_step_kernel<Cfg>,
-                                                               Cfg::BLOCK, Cfg::SMEM_BYTES));
-        if (s.occ < 1) return fail(SGB_ERR_CUDA, "step kernel does not fit on an SM");
+        int rc0;
+        if ((rc0 = prepare_step_kernel<float>(&s.occ))) return rc0;
+        if ((rc0 = prepare_step_kernel<__half>(&s.occ_h))) return rc0;
+        if ((rc0 = prepare_step_kernel<__nv_bfloat16>(&s.occ_b))) return rc0;
         CUDA_TRY(cudaGetSymbolAddress((void **)&s.err, g_dev_err));
         cudaMemPoolProps props;
         memset(&props, 0, sizeof props);
@@ -225,14 +241,32 @@ void fill_step_constants(const sgb_grid *g, const sgb_layout_info &L, StepArgs &
     a.inv_vol = (float)(1.0 / ((double)g->dx * g->dy * g->dz));
 }
 
-int encode_map(CUtensorMap *map, const float *padded, const sgb_layout_info &L, int box_x, int box_y)
+template <class T>
+struct TmaType;
+template <>
+struct TmaType<float> {
+    static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+};
+template <>
+struct TmaType<__half> {
+    static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+};
+template <>
+struct TmaType<__nv_bfloat16> {
+    static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+};
+
+// 3D tiled map over the computed region of a padded field of element type T.
+template <class T>
+int encode_map(CUtensorMap *map, const void *padded, const sgb_layout_info &L, int box_x, int box_y)
 {
-    void *base = const_cast<float *>(padded) + L.origin;
+    const size_t es = sizeof(T);
+    void *base = const_cast<char *>(static_cast<const char *>(padded)) + L.origin * es;
     cuuint64_t dims[3] = {(cuuint64_t)L.Nx, (cuuint64_t)L.Ny, (cuuint64_t)L.Nz};
-    cuuint64_t strides[2] = {(cuuint64_t)(L.sx * 4), (cuuint64_t)(L.stride_z * 4)};
+    cuuint64_t strides[2] = {(cuuint64_t)(L.sx * es), (cuuint64_t)(L.stride_z * es)};
     cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, TmaType<T>::v, 3, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           SGB_L2PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -243,22 +277,25 @@ struct StepMaps {
     CUtensorMap ucur, ucur_in, uprev, m, phi;
 };
 
-int encode_step_maps(StepMaps &mp, const float *u_cur, const float *u_prev, const float *m,
+template <class T>
+int encode_step_maps(StepMaps &mp, const void *u_cur, const void *u_prev, const float *m,
                      const float *phi, const sgb_layout_info &L)
 {
+    using G = Stage<Cfg, T>;
     int rc;
-    if ((rc = encode_map(&mp.ucur, u_cur, L, Cfg::SW, Cfg::SH))) return rc;
-    if ((rc = encode_map(&mp.ucur_in, u_cur, L, Cfg::BX, Cfg::BY))) return rc;
-    if ((rc = encode_map(&mp.uprev, u_prev, L, Cfg::BX, Cfg::BY))) return rc;
-    if ((rc = encode_map(&mp.m, m, L, Cfg::BX, Cfg::BY))) return rc;
-    if ((rc = encode_map(&mp.phi, phi ? phi : u_prev, L, Cfg::BX, Cfg::BY))) return rc;
+    if ((rc = encode_map<T>(&mp.ucur, u_cur, L, G::SW, Cfg::SH))) return rc;
+    if ((rc = encode_map<T>(&mp.ucur_in, u_cur, L, Cfg::BX, Cfg::BY))) return rc;
+    if ((rc = encode_map<T>(&mp.uprev, u_prev, L, Cfg::BX, Cfg::BY))) return rc;
+    if ((rc = encode_map<float>(&mp.m, m, L, Cfg::BX, Cfg::BY))) return rc;
+    if ((rc = encode_map<float>(&mp.phi, phi ? phi : m, L, Cfg::BX, Cfg::BY))) return rc;
     return SGB_OK;
 }
 
+template <class T>
 int launch_step(const StepArgs &a, const StepMaps &mp, int grid, cudaStream_t st)
 {
-    fused_step_kernel<Cfg><<<grid, Cfg::BLOCK, Cfg::SMEM_BYTES, st>>>(a, mp.ucur, mp.ucur_in, mp.uprev, mp.m,
-                                                                       mp.phi);
+    fused_step_kernel<Cfg, T><<<grid, Cfg::BLOCK, Stage<Cfg, T>::SMEM_BYTES, st>>>(
+        a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi);
     CUDA_TRY(cudaGetLastError());
     ++t_launches;
     return SGB_OK;
@@ -432,8 +469,8 @@ extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_t
 
     StepArgs a;
     fill_step_constants(g, L, a);
-    a.u_out = static_cast<float *>(u_prev_to_next);
-    a.u_cur = static_cast<const float *>(u_cur);
+    a.u_out = u_prev_to_next;
+    a.u_cur = u_cur;
     a.phi = phi;
     a.err = ds->err;
     a.step_add = step;
@@ -446,8 +483,8 @@ extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_t
     int grid = 0;
     choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, ds->occ, a, &grid);
     StepMaps mp;
-    if ((rc = encode_step_maps(mp, a.u_cur, a.u_out, m, phi, L))) return rc;
-    if ((rc = launch_step(a, mp, grid, st))) return rc;
+    if ((rc = encode_step_maps<float>(mp, a.u_cur, a.u_out, m, phi, L))) return rc;
+    if ((rc = launch_step<float>(a, mp, grid, st))) return rc;
     if (rec && rec->nrec > 0) {
         std::vector<long long> off(rec->nrec);
         for (int r = 0; r < rec->nrec; ++r)
@@ -469,6 +506,139 @@ extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_t
     return SGB_OK;
 }
 
+namespace {
+
+// Shot time loop and outputs for wavefield storage T (run_shot after its
+// argument checks and the CFL check).
+template <class T>
+int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
+               Scratch &sc, const float *d_vel, const float *d_wav, int nt,
+               const int32_t *src_ijk, int nrec, const long long *d_off, float *d_tr,
+               float *final_u)
+{
+    int rc;
+    const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
+    const size_t ubytes = (size_t)L.elems * sizeof(T), fbytes = (size_t)L.elems * 4;
+    void *u0, *u1;
+    float *phi, *m;
+    ScaleState *ss = nullptr;
+    int *d_step;
+    if ((rc = sc.get(&u0, ubytes)) || (rc = sc.get(&u1, ubytes)) ||
+        (rc = sc.get((void **)&phi, fbytes)) || (rc = sc.get((void **)&m, fbytes)) ||
+        (rc = sc.get((void **)&d_step, sizeof(int))))
+        return rc;
+    CUDA_TRY(cudaMemsetAsync(d_step, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(u0, 0, ubytes, st));
+    CUDA_TRY(cudaMemsetAsync(u1, 0, ubytes, st));
+    CUDA_TRY(cudaMemsetAsync(phi, 0, fbytes, st));
+    CUDA_TRY(cudaMemsetAsync(m, 0, fbytes, st));
+    if (Elem<T>::SCALED) {
+        if ((rc = sc.get((void **)&ss, sizeof(ScaleState)))) return rc;
+        static const ScaleState init = {{1.0f, 1.0f, 1.0f, 1.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+        CUDA_TRY(cudaMemcpyAsync(ss, &init, sizeof init, cudaMemcpyHostToDevice, st));
+    }
+    make_m_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), d_vel, g->dt, m);
+    CUDA_TRY(cudaGetLastError());
+    ++t_launches;
+
+    // buf[0] holds u^{-1}, buf[1] holds u^0; step n reads buf[(n+1)&1] and
+    // overwrites buf[n&1] with u^{n+1}.
+    void *buf[2] = {u0, u1};
+    StepArgs base;
+    fill_step_constants(g, L, base);
+    base.phi = phi;
+    base.err = ds->err;
+    base.scale = ss;
+    if (src_ijk) {
+        base.si = src_ijk[0];
+        base.sj = src_ijk[1];
+        base.sk = src_ijk[2];
+        base.wavelet = d_wav;
+        base.m_src = m + L.origin + (long long)src_ijk[2] * L.stride_z +
+                     (long long)src_ijk[1] * L.sx + src_ijk[0];
+    }
+    base.nrec = nrec;
+    base.rec_off = d_off;
+    base.traces = d_tr;
+    const int occ = std::is_same<T, float>::value ? ds->occ
+                    : std::is_same<T, __half>::value ? ds->occ_h : ds->occ_b;
+    int grid = 0;
+    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, occ, base, &grid);
+    StepMaps maps[2];  // [parity of n]
+    for (int p = 0; p < 2; ++p)
+        if ((rc = encode_step_maps<T>(maps[p], buf[(p + 1) & 1], buf[p & 1], m, phi, L))) return rc;
+
+    auto args_for = [&](int parity, const int *step_ptr, int step_add) {
+        StepArgs a = base;
+        a.u_out = buf[parity & 1];
+        a.u_cur = buf[(parity + 1) & 1];
+        a.step_ptr = step_ptr;
+        a.step_add = step_add;
+        return a;
+    };
+
+    const int GS = 32;  // steps per graph replay (even: the buffer parity repeats)
+    const int replays = nt / GS;
+    if (replays > 0) {
+        cudaStream_t cs;
+        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int crc = SGB_OK;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            for (int i = 0; i < GS && crc == SGB_OK; ++i)
+                crc = launch_step<T>(args_for(i, d_step, i), maps[i & 1], grid, cs);
+            if (crc == SGB_OK) {
+                advance_kernel<<<1, 32, 0, cs>>>(d_step, GS);
+                ce = cudaGetLastError();
+            }
+            cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+            if (ce == cudaSuccess) ce = ee;
+        }
+        t_launches -= GS;  // captured launches are counted at replay
+        if (ce == cudaSuccess && crc == SGB_OK) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce == cudaSuccess && crc == SGB_OK) {
+            for (int r = 0; r < replays && ce == cudaSuccess; ++r) {
+                ce = cudaGraphLaunch(exec, st);
+                t_launches += GS + 1;
+            }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (crc) return crc;
+        CUDA_TRY(ce);
+    }
+    for (int n = replays * GS; n < nt; ++n)
+        if ((rc = launch_step<T>(args_for(n, nullptr, n), maps[n & 1], grid, st))) return rc;
+
+    // u^{nt}: written by step nt-1 into buf[(nt-1)&1] (u^0 = buf[1] when nt = 0)
+    const void *u_final_dev = nt > 0 ? buf[(nt - 1) & 1] : buf[1];
+    const float *s_final = ss ? &ss->s[nt & 3] : nullptr;
+    if (nrec > 0 && nt > 0) {
+        gather_t_kernel<T><<<(nrec + 255) / 256, 256, 0, st>>>(
+            static_cast<const T *>(u_final_dev), d_off, nrec, s_final,
+            d_tr + (size_t)(nt - 1) * nrec, ds->err);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+    }
+    if (final_u) {
+        const bool host_u = !is_device_ptr(final_u);
+        float *dst = final_u;
+        if (host_u && (rc = sc.get((void **)&dst, (size_t)ncomp * 4))) return rc;
+        unpack_t_kernel<T><<<ew_grid(ncomp, *ds), 256, 0, st>>>(
+            pad_geom(L), static_cast<const T *>(u_final_dev), s_final, dst);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+        if (host_u)
+            CUDA_TRY(cudaMemcpyAsync(final_u, dst, (size_t)ncomp * 4, cudaMemcpyDeviceToHost, st));
+    }
+    return SGB_OK;
+}
+
+}  // namespace
+
 extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
                         const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec,
                         float *traces, float *final_u, void *stream)
@@ -476,7 +646,6 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     sgb_layout_info L;
     int rc = check_grid(g, &L);
     if (rc) return rc;
-    if (g->storage != SGB_FP32) return fail(SGB_ERR_INVALID_ARG, "run_shot: only SGB_FP32 here");
     if (!velocity) return fail(SGB_ERR_INVALID_ARG, "velocity is NULL");
     if (nt < 0) return fail(SGB_ERR_INVALID_ARG, "nt must be >= 0");
     if (nt > 0 && src_ijk && !wavelet) return fail(SGB_ERR_INVALID_ARG, "wavelet is NULL");
@@ -497,17 +666,12 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     if ((rc = device_state(&ds))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
-    const size_t fbytes = (size_t)L.elems * 4;
     {
         int pending = 0;
         if ((rc = read_and_clear_dev_err(*ds, st, &pending))) return rc;
     }
 
     Scratch sc{st, ds->pool, {}};
-    float *u0, *u1, *phi, *m;
-    if ((rc = sc.get((void **)&u0, fbytes)) || (rc = sc.get((void **)&u1, fbytes)) ||
-        (rc = sc.get((void **)&phi, fbytes)) || (rc = sc.get((void **)&m, fbytes)))
-        return rc;
     const float *d_vel = velocity;
     if (!is_device_ptr(velocity)) {
         float *t;
@@ -550,104 +714,20 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
         if ((rc = sc.get((void **)&d_off, (size_t)nrec * 8))) return rc;
         CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), (size_t)nrec * 8, cudaMemcpyHostToDevice, st));
     }
-    int *d_step;
-    if ((rc = sc.get((void **)&d_step, sizeof(int)))) return rc;
-    CUDA_TRY(cudaMemsetAsync(d_step, 0, sizeof(int), st));
-    CUDA_TRY(cudaMemsetAsync(u0, 0, fbytes, st));
-    CUDA_TRY(cudaMemsetAsync(u1, 0, fbytes, st));
-    CUDA_TRY(cudaMemsetAsync(phi, 0, fbytes, st));
-    CUDA_TRY(cudaMemsetAsync(m, 0, fbytes, st));
-    make_m_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), d_vel, g->dt, m);
-    CUDA_TRY(cudaGetLastError());
-    ++t_launches;
-
-    // buf[0] holds u^{-1}, buf[1] holds u^0; step n reads buf[(n+1)&1] and
-    // overwrites buf[n&1] with u^{n+1}.
-    float *buf[2] = {u0, u1};
-    StepArgs base;
-    fill_step_constants(g, L, base);
-    base.phi = phi;
-    base.err = ds->err;
-    if (src_ijk) {
-        base.si = src_ijk[0];
-        base.sj = src_ijk[1];
-        base.sk = src_ijk[2];
-        base.wavelet = d_wav;
+    switch (g->storage) {
+    case SGB_FP16_SCALED:
+        rc = run_shot_t<__half>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u);
+        break;
+    case SGB_BF16:
+        rc = run_shot_t<__nv_bfloat16>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
+                                       final_u);
+        break;
+    default:
+        rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u);
     }
-    base.nrec = nrec;
-    base.rec_off = d_off;
-    base.traces = d_tr;
-    int grid = 0;
-    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, ds->occ, base, &grid);
-    StepMaps maps[2];  // [parity of n]
-    for (int p = 0; p < 2; ++p)
-        if ((rc = encode_step_maps(maps[p], buf[(p + 1) & 1], buf[p & 1], m, phi, L))) return rc;
-
-    auto args_for = [&](int parity, const int *step_ptr, int step_add) {
-        StepArgs a = base;
-        a.u_out = buf[parity & 1];
-        a.u_cur = buf[(parity + 1) & 1];
-        a.step_ptr = step_ptr;
-        a.step_add = step_add;
-        return a;
-    };
-
-    const int G = 32;  // steps per graph replay (even: the buffer parity repeats)
-    const int replays = nt / G;
-    if (replays > 0) {
-        cudaStream_t cs;
-        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        int crc = SGB_OK;
-        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (ce == cudaSuccess) {
-            for (int i = 0; i < G && crc == SGB_OK; ++i)
-                crc = launch_step(args_for(i, d_step, i), maps[i & 1], grid, cs);
-            if (crc == SGB_OK) {
-                advance_kernel<<<1, 32, 0, cs>>>(d_step, G);
-                ce = cudaGetLastError();
-            }
-            cudaError_t ee = cudaStreamEndCapture(cs, &graph);
-            if (ce == cudaSuccess) ce = ee;
-        }
-        t_launches -= G;  // captured launches are counted at replay
-        if (ce == cudaSuccess && crc == SGB_OK) ce = cudaGraphInstantiate(&exec, graph, 0);
-        if (ce == cudaSuccess && crc == SGB_OK) {
-            for (int r = 0; r < replays && ce == cudaSuccess; ++r) {
-                ce = cudaGraphLaunch(exec, st);
-                t_launches += G + 1;
-            }
-        }
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-        if (crc) return crc;
-        CUDA_TRY(ce);
-    }
-    for (int n = replays * G; n < nt; ++n)
-        if ((rc = launch_step(args_for(n, nullptr, n), maps[n & 1], grid, st))) return rc;
-
-    float *u_final_dev = buf[(nt + 1) & 1];  // u^{nt}: written by step nt-1 into buf[(nt-1)&1]
-    if (nt > 0) u_final_dev = buf[(nt - 1) & 1];
-    if (nrec > 0 && nt > 0) {
-        gather_kernel<<<(nrec + 255) / 256, 256, 0, st>>>(u_final_dev, d_off, nrec,
-                                                          d_tr + (size_t)(nt - 1) * nrec, ds->err);
-        CUDA_TRY(cudaGetLastError());
-        ++t_launches;
-        if (host_traces)
-            CUDA_TRY(cudaMemcpyAsync(traces, d_tr, (size_t)nt * nrec * 4, cudaMemcpyDeviceToHost, st));
-    }
-    if (final_u) {
-        const bool host_u = !is_device_ptr(final_u);
-        float *dst = final_u;
-        if (host_u && (rc = sc.get((void **)&dst, (size_t)ncomp * 4))) return rc;
-        unpack_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), u_final_dev, dst);
-        CUDA_TRY(cudaGetLastError());
-        ++t_launches;
-        if (host_u)
-            CUDA_TRY(cudaMemcpyAsync(final_u, dst, (size_t)ncomp * 4, cudaMemcpyDeviceToHost, st));
-    }
+    if (rc) return rc;
+    if (host_traces && nt > 0)
+        CUDA_TRY(cudaMemcpyAsync(traces, d_tr, (size_t)nt * nrec * 4, cudaMemcpyDeviceToHost, st));
     int dev_err = 0;
     if ((rc = read_and_clear_dev_err(*ds, st, &dev_err))) return rc;
     if (dev_err & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a step kernel wait timed out");
@@ -694,12 +774,8 @@ int noalloc_setup(NoAllocState **out)
         CUDA_TRY(cudaGetSymbolAddress((void **)&s.scratch, g_noalloc_scratch));
         CUDA_TRY(cudaGetSymbolAddress((void **)&s.err, g_dev_err));
         CUDA_TRY(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev));
-        CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel<Cfg>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)Cfg::SMEM_BYTES));
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.occ, fused_step_kernel<Cfg>,
-                                                               Cfg::BLOCK, Cfg::SMEM_BYTES));
-        if (s.occ < 1) return fail(SGB_ERR_CUDA, "step kernel does not fit on an SM");
+        int rc0;
+        if ((rc0 = prepare_step_kernel<float>(&s.occ))) return rc0;
         if (!g_encode) {
             cudaDriverEntryPointQueryResult q;
             void *fn = nullptr;
@@ -826,14 +902,14 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
     choose_decomposition(L.Nx, L.Ny, L.Nz, ns->sms, ns->occ, base_args, &grid);
     StepMaps maps[2];
     for (int p = 0; p < 2; ++p)
-        if ((rc = encode_step_maps(maps[p], buf[(p + 1) & 1], buf[p & 1], m, phi, L))) return rc;
+        if ((rc = encode_step_maps<float>(maps[p], buf[(p + 1) & 1], buf[p & 1], m, phi, L))) return rc;
     for (int n = 0; n < nt; ++n) {
         StepArgs a = base_args;
         a.u_out = buf[n & 1];
         a.u_cur = buf[(n + 1) & 1];
         a.step_ptr = nullptr;
         a.step_add = n;
-        if ((rc = launch_step(a, maps[n & 1], grid, st))) return rc;
+        if ((rc = launch_step<float>(a, maps[n & 1], grid, st))) return rc;
     }
     float *u_last = nt > 0 ? buf[(nt - 1) & 1] : buf[1];
     if (nrec > 0 && nt > 0) {

@@ -1,4 +1,6 @@
-// Fused 25-point wave step with in-launch PML, FP32 storage (sm_103a).
+// Fused 25-point wave step with in-launch PML (sm_103a), templated on the
+// wavefield storage type: fp32, fp16 with a per-field power-of-two scale, or
+// bf16; the arithmetic is fp32 in every case.
 //
 // What it computes (arXiv 2009.04619, section III-A): one leapfrog step of
 // Eq. 2, u^{n+1} = 2u^n - u^{n-1} + m L u^n with m = V^2 dt^2 and L the
@@ -41,8 +43,17 @@
 //  - eta and its central differences are evaluated in closed form from the
 //    integer depth into the layer: no eta array is read;
 //  - every mbarrier wait is bounded (2 s); on timeout the CTA records
-//    DEV_ERR_TIMEOUT, drains its own copies (bounded) and exits.
+//    DEV_ERR_TIMEOUT, drains its own copies (bounded) and exits;
+//  - 16-bit storage keeps only the two wavefields in 16 bits (m and phi stay
+//    fp32).  The Laplacian is accumulated on the stored values and multiplied
+//    by the field's scale once.  The fp16 scale of u^{n+1} is a power of two
+//    chosen in the kernel from max|u^n|, max|u^{n-1}| and the injected
+//    amplitude, so that |u^{n+1}| / scale < 2^14 (fp16 max 65504); every CTA
+//    also contributes max|u^{n+1}| (warp max + atomicMax) for the next step.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ptx.cuh"
 
 namespace sgb {
@@ -53,10 +64,17 @@ constexpr int HALO = 4;       // zero points before y = 0, z = 0 and after every
 
 enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_RANGE = 4 };
 
+// Scale state of a 16-bit wavefield pair (device memory): s[k & 3] is the
+// scale of u^k (stored value = u^k / s), mx[k & 3] is max |u^k|.
+struct ScaleState {
+    float s[4];
+    float mx[4];
+};
+
 struct StepArgs {
-    float *u_out;          // padded base: holds u^{n-1} on entry, u^{n+1} on exit
-    const float *u_cur;    // padded base of u^n (receiver pre-sampling only)
-    float *phi;            // padded base of phi (PML auxiliary field)
+    void *u_out;           // padded base: holds u^{n-1} on entry, u^{n+1} on exit
+    const void *u_cur;     // padded base of u^n (receiver pre-sampling only)
+    float *phi;            // padded base of phi (PML auxiliary field, fp32)
     int Nx, Ny, Nz;        // computed extents
     int nb, nx, ny, nz;    // PML width, inner extents
     long long sx, sxy;     // element strides of y and z
@@ -67,15 +85,135 @@ struct StepArgs {
     float kx, ky, kz;      // dt d(eta)/da d(u)/da = k (d(+1)^2 - d(-1)^2) (u(+1) - u(-1))
     int si, sj, sk;        // source point (sk < 0: none)
     const float *wavelet;  // w(n dt) samples
+    const float *m_src;    // m at the source point (fp16 scale bound)
     float inv_vol;         // 1 / (dx dy dz)
     const int *step_ptr;   // device step counter (graph replays) or null
     int step_add;          // n = *step_ptr + step_add
     int nrec;              // receivers sampled from u^n into row n - 1 (n >= 1)
     const long long *rec_off;
     float *traces;
+    ScaleState *scale;     // fp16 storage only
     int *err;              // device error word
     int tiles_x, tiles_y, zc;
 };
+
+// Counter-based hash (Murmur3 finaliser) of a point index and a step: the random
+// bits of stochastic rounding, reproducible run to run.
+__device__ __forceinline__ uint32_t hash_bits(uint32_t a, uint32_t b)
+{
+    uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Stochastic rounding of x to a format that keeps the top (32 - drop) bits of
+// the fp32 pattern: add random bits below the kept ones, then truncate.  With
+// round-to-nearest, the rounding errors of a smooth field repeat from step to
+// step and add up coherently over a run; stochastic rounding makes them
+// uncorrelated (zero mean), so they grow like a random walk instead.
+template <int DROP>
+__device__ __forceinline__ float sr_bits(float x, uint32_t rnd)
+{
+    const uint32_t b = __float_as_uint(x);
+    if ((b & 0x7F800000u) == 0x7F800000u) return x;  // Inf / NaN unchanged
+    return __uint_as_float(b + (rnd & ((1u << DROP) - 1u)));
+}
+
+// Storage traits: TMA x margin (16 bytes), 4-wide loads from shared memory and
+// stores to global memory (rnd: random bits for stochastic rounding), scalar
+// access.
+template <class T>
+struct Elem;
+
+template <>
+struct Elem<float> {
+    static constexpr int HX = 4;
+    static constexpr bool SCALED = false;
+    __device__ static __forceinline__ float4 ld(const float *p) { return lds128(p); }
+    __device__ static __forceinline__ void st(float *p, float4 v, uint32_t) { stg128(p, v); }
+    __device__ static __forceinline__ float get(const float *p) { return *p; }
+    __device__ static __forceinline__ void put(float *p, float v, uint32_t) { *p = v; }
+};
+
+template <>
+struct Elem<__half> {
+    static constexpr int HX = 8;
+    static constexpr bool SCALED = true;
+    __device__ static __forceinline__ float4 ld(const __half *p)
+    {
+        const uint2 r = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ static __forceinline__ __half2 pack(float x, float y, uint32_t rnd)
+    {
+#ifdef SGB_16BIT_RN
+        (void)rnd;
+        return __floats2half2_rn(x, y);
+#else
+        // fp16 keeps 10 of fp32's 23 mantissa bits (normal range): drop 13
+        return __halves2half2(__float2half_rz(sr_bits<13>(x, rnd)),
+                              __float2half_rz(sr_bits<13>(y, rnd >> 13)));
+#endif
+    }
+    __device__ static __forceinline__ void st(__half *p, float4 v, uint32_t rnd)
+    {
+        __half2 a = pack(v.x, v.y, rnd), b = pack(v.z, v.w, hash_bits(rnd, 0x51u));
+        uint2 r;
+        r.x = *reinterpret_cast<uint32_t *>(&a);
+        r.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = r;
+    }
+    __device__ static __forceinline__ float get(const __half *p) { return __half2float(*p); }
+    __device__ static __forceinline__ void put(__half *p, float v, uint32_t rnd)
+    {
+        *p = pack(v, v, rnd).x;
+    }
+};
+
+template <>
+struct Elem<__nv_bfloat16> {
+    static constexpr int HX = 8;
+    static constexpr bool SCALED = false;
+    __device__ static __forceinline__ float4 ld(const __nv_bfloat16 *p)
+    {
+        const uint2 r = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ static __forceinline__ __nv_bfloat162 pack(float x, float y, uint32_t rnd)
+    {
+#ifdef SGB_16BIT_RN
+        (void)rnd;
+        return __floats2bfloat162_rn(x, y);
+#else
+        // bf16 is the top 16 bits of fp32: drop 16
+        return __halves2bfloat162(__float2bfloat16_rz(sr_bits<16>(x, rnd)),
+                                  __float2bfloat16_rz(sr_bits<16>(y, rnd >> 16)));
+#endif
+    }
+    __device__ static __forceinline__ void st(__nv_bfloat16 *p, float4 v, uint32_t rnd)
+    {
+        __nv_bfloat162 a = pack(v.x, v.y, rnd), b = pack(v.z, v.w, hash_bits(rnd, 0x51u));
+        uint2 r;
+        r.x = *reinterpret_cast<uint32_t *>(&a);
+        r.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = r;
+    }
+    __device__ static __forceinline__ float get(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ void put(__nv_bfloat16 *p, float v, uint32_t rnd)
+    {
+        *p = pack(v, v, rnd).x;
+    }
+};
+
+constexpr int align128(int b) { return (b + 127) / 128 * 128; }
 
 template <int TXT_, int TYT_, int TY_, int NU_, int NP_, int MINB_, int U_>
 struct TileCfg {
@@ -85,31 +223,35 @@ struct TileCfg {
     static constexpr int THREADS = TXT * TYT;   // consumer (compute) threads
     static constexpr int BLOCK = THREADS + 32;  // plus one producer warp
     static constexpr int BX = 4 * TXT, BY = TY * TYT;
-    static constexpr int HX = 4;  // x margin of the u^n box: 16 bytes keeps TMA x aligned
-    static constexpr int SW = BX + 2 * HX;
     static constexpr int SH = BY + 2 * R;
-    static constexpr int U_STAGE = SW * SH;
     static constexpr int P_TILE = BX * BY;
-    static constexpr int P_STAGE = 3 * P_TILE;
     static constexpr int WARPS = THREADS / 32;
-    static constexpr size_t SMEM_BYTES =
-        size_t(NU * U_STAGE + NP * P_STAGE) * 4 + size_t(NU + NP) * 16 + size_t(NU + NP + 1) * 4;
     static_assert(NU >= 8, "the u ring must hold the 8 planes that prime the register queue");
     static_assert(U_ >= 1 && U_ <= 9, "unroll factor");
     static_assert(NP >= 2 && THREADS % 32 == 0, "ring sizes");
-    static_assert((U_STAGE * 4) % 128 == 0 && (P_TILE * 4) % 128 == 0, "stage alignment");
-    static_assert(SW <= 256 && SH <= 256 && BX <= 256 && BY <= 256, "TMA box limits");
+    static_assert(SH <= 256 && BX <= 240 && BY <= 256, "TMA box limits");
+};
+
+// Shared-memory geometry of a configuration for storage type T (bytes).
+template <class C, class T>
+struct Stage {
+    static constexpr int HX = Elem<T>::HX;         // x margin of the u^n box
+    static constexpr int SW = C::BX + 2 * HX;      // u^n box width (elements)
+    static constexpr int U_BYTES = align128(SW * C::SH * (int)sizeof(T));
+    static constexpr int UP_BYTES = align128(C::P_TILE * (int)sizeof(T));
+    static constexpr int F_BYTES = C::P_TILE * 4;  // one fp32 tile (m or phi)
+    static constexpr int P_BYTES = UP_BYTES + 2 * F_BYTES;
+    static constexpr size_t SMEM_BYTES = size_t(C::NU) * U_BYTES + size_t(C::NP) * P_BYTES +
+                                         size_t(C::NU + C::NP) * 16 +
+                                         size_t(C::NU + C::NP + 1) * 4;
+    static_assert(U_BYTES % 128 == 0 && F_BYTES % 128 == 0, "stage alignment");
+    static_assert(SW <= 256, "TMA box limit");
 };
 
 // Depth (points) of index i into the PML along one axis; 0 in the inner range.
 __device__ __forceinline__ int pml_depth(int n_inner, int nb, int i)
 {
     return max(max(nb - i, i - (nb + n_inner - 1)), 0);
-}
-
-__device__ __forceinline__ float interior_update(float c, float up, float mm, float L)
-{
-    return fmaf(mm, L, fmaf(2.0f, c, -up));
 }
 
 __device__ __forceinline__ float f4get(const float4 &v, int e)
@@ -159,26 +301,28 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-
-
-
 // Per-thread state of one fused-step work unit (a tile x a z-chunk).
-template <class C>
+template <class C, class T>
 struct StepCta {
+    using E = Elem<T>;
+    using G = Stage<C, T>;
+    static constexpr bool SCALED = E::SCALED;
     static constexpr int TXT = C::TXT, TY = C::TY, NU = C::NU, NP = C::NP;
     static constexpr int THREADS = C::THREADS, QN = C::QN, U = C::U, WARPS = C::WARPS;
-    static constexpr int BX = C::BX, BY = C::BY, HX = C::HX, SW = C::SW;
-    static constexpr int U_STAGE = C::U_STAGE, P_TILE = C::P_TILE, P_STAGE = C::P_STAGE;
+    static constexpr int BX = C::BX, BY = C::BY, HX = G::HX, SW = G::SW;
+    static constexpr int P_TILE = C::P_TILE;
     static constexpr uint64_t WAIT_NS = 2000000000ull;
 
     const StepArgs *pa;  // the kernel argument, in the constant parameter space
     const CUtensorMap *tm_ucur, *tm_ucur_in, *tm_uprev, *tm_m, *tm_phi;
-    float *su, *sp;
+    unsigned char *su, *sp;  // u ring, (u^{n-1}, m, phi) ring
     uint64_t *full_u, *empty_u, *full_p, *empty_p;
     int *lastf_u, *lastf_p, *s_abort;
     long long base_off;  // element offset of (gi, gj0, k = 0)
     int tid, lane, x0, y0, z0, z1, n, row0, colu, gi, gj0, prow;
     bool xy_inner, aborted, store_ok;
+    float s_cur, s_prev, inv_s_next;  // fp16 scales (1 otherwise)
+    float vmax;                       // running max |u^{n+1}| of this thread
 
     __device__ __forceinline__ bool plane_pml(int k) const
     {
@@ -193,10 +337,15 @@ struct StepCta {
         }
     }
 
+    __device__ __forceinline__ const T *ustage(int s) const
+    {
+        return reinterpret_cast<const T *>(su + s * G::U_BYTES);
+    }
+
     // Planes outside the chunk feed only the z-queue: no x-y halo needed.
     __device__ __forceinline__ bool front_only(int p) const { return p < z0 || p >= z1; }
 
-    // Offset, inside a u stage holding plane p, of this thread's row-r float4.
+    // Offset, inside a u stage holding plane p, of this thread's row-r quad.
     __device__ __forceinline__ int own_off(int p, int r) const
     {
         return front_only(p) ? prow + r * BX : (row0 + r) * SW + colu;
@@ -209,11 +358,11 @@ struct StepCta {
         if (f > 0) wait(empty_u + s, (f - 1) & 1);  // previous plane of the slot released
         lastf_u[s] = f;
         if (front_only(p)) {
-            mbar_arrive_expect_tx(full_u + s, P_TILE * 4);
-            tma_load_3d(su + s * U_STAGE, tm_ucur_in, full_u + s, x0, y0, p);
+            mbar_arrive_expect_tx(full_u + s, P_TILE * (int)sizeof(T));
+            tma_load_3d(su + s * G::U_BYTES, tm_ucur_in, full_u + s, x0, y0, p);
         } else {
-            mbar_arrive_expect_tx(full_u + s, U_STAGE * 4);
-            tma_load_3d(su + s * U_STAGE, tm_ucur, full_u + s, x0 - HX, y0 - R, p);
+            mbar_arrive_expect_tx(full_u + s, SW * C::SH * (int)sizeof(T));
+            tma_load_3d(su + s * G::U_BYTES, tm_ucur, full_u + s, x0 - HX, y0 - R, p);
         }
     }
 
@@ -224,18 +373,12 @@ struct StepCta {
         if (f > 0) wait(empty_p + s, (f - 1) & 1);
         lastf_p[s] = f;
         const bool pml = plane_pml(k);
-        mbar_arrive_expect_tx(full_p + s, (pml ? 3 : 2) * P_TILE * 4);
-        float *d = sp + s * P_STAGE;
-#ifndef SGB_NO_HINT
+        mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + (pml ? 2 : 1) * G::F_BYTES);
+        unsigned char *d = sp + s * G::P_BYTES;
         const uint64_t pol = policy_evict_first();
         tma_load_3d_hint(d, tm_uprev, full_p + s, x0, y0, k, pol);
-        tma_load_3d_hint(d + P_TILE, tm_m, full_p + s, x0, y0, k, pol);
-        if (pml) tma_load_3d_hint(d + 2 * P_TILE, tm_phi, full_p + s, x0, y0, k, pol);
-#else
-        tma_load_3d(d, tm_uprev, full_p + s, x0, y0, k);
-        tma_load_3d(d + P_TILE, tm_m, full_p + s, x0, y0, k);
-        if (pml) tma_load_3d(d + 2 * P_TILE, tm_phi, full_p + s, x0, y0, k);
-#endif
+        tma_load_3d_hint(d + G::UP_BYTES, tm_m, full_p + s, x0, y0, k, pol);
+        if (pml) tma_load_3d_hint(d + G::UP_BYTES + G::F_BYTES, tm_phi, full_p + s, x0, y0, k, pol);
     }
 
     // Producer lane: every plane of u^n (z0-4 .. z1+3) and every (u^{n-1}, m,
@@ -261,6 +404,7 @@ struct StepCta {
 
     // One z-plane: iteration it (plane k = z0 + it).  The queue holds planes
     // k-4 .. k+3 at q[O .. O+7]; the front plane k+4 is loaded into q[O+8].
+    // Queue values are the stored (scaled) values; true u = stored * s_cur.
     template <int O, bool PML>
     __device__ __forceinline__ void plane(float4 (&q)[TY][QN], int it)
     {
@@ -270,12 +414,15 @@ struct StepCta {
         const int sf = relf % NU;
         wait(full_u + sf, (relf / NU) & 1);
 #pragma unroll
-        for (int r = 0; r < TY; ++r) q[r][O + 8] = lds128(su + sf * U_STAGE + own_off(k + 4, r));
+        for (int r = 0; r < TY; ++r) q[r][O + 8] = E::ld(ustage(sf) + own_off(k + 4, r));
         const int sq = it % NP;
         wait(full_p + sq, (it / NP) & 1);
         const int sc = (it + 4) % NU;
-        const float *cu = su + sc * U_STAGE;
-        const float *pu = sp + sq * P_STAGE;
+        const T *cu = ustage(sc);
+        const unsigned char *pu = sp + sq * G::P_BYTES;
+        const T *pup = reinterpret_cast<const T *>(pu);
+        const float *pm = reinterpret_cast<const float *>(pu + G::UP_BYTES);
+        const float *pph = reinterpret_cast<const float *>(pu + G::UP_BYTES + G::F_BYTES);
 
         // 25-point Laplacian (Eq. 3): centre and z part from the queue
         float4 L[TY], gy[TY];
@@ -293,7 +440,7 @@ struct StepCta {
         for (int d = -R; d < TY + R; ++d) {
             float4 v;
             if (d >= 0 && d < TY) v = q[d][O + 4];
-            else v = lds128(cu + (row0 + d) * SW + colu);
+            else v = E::ld(cu + (row0 + d) * SW + colu);
 #pragma unroll
             for (int r = 0; r < TY; ++r) {
                 const int m = d > r ? d - r : r - d;
@@ -314,9 +461,9 @@ struct StepCta {
         const long long off0 = base_off + (long long)k * a.sxy;
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
-            const float *rowp = cu + (row0 + r) * SW + colu;
-            const float4 c = q[r][O + 4];
-            const float4 lf = lds128(rowp - 4), rt = lds128(rowp + 4);
+            const T *rowp = cu + (row0 + r) * SW + colu;
+            float4 c = q[r][O + 4];
+            const float4 lf = E::ld(rowp - 4), rt = E::ld(rowp + 4);
             const float w[12] = {lf.x, lf.y, lf.z, lf.w, c.x, c.y, c.z, c.w,
                                  rt.x, rt.y, rt.z, rt.w};
             float4 Lr = L[r];
@@ -331,18 +478,23 @@ struct StepCta {
                 f4set(Lr, e, sacc);
             }
             const int pr = prow + r * BX;
-            const float4 up = lds128(pu + pr);
-            const float4 mm = lds128(pu + P_TILE + pr);
+            float4 up = E::ld(pup + pr);
+            const float4 mm = lds128(pm + pr);
+            if constexpr (SCALED) {  // stored values -> true values
+                Lr = f4mul(s_cur, Lr);
+                c = f4mul(s_cur, c);
+                up = f4mul(s_prev, up);
+            }
             float4 un;
-            un.x = interior_update(c.x, up.x, mm.x, Lr.x);
-            un.y = interior_update(c.y, up.y, mm.y, Lr.y);
-            un.z = interior_update(c.z, up.z, mm.z, Lr.z);
-            un.w = interior_update(c.w, up.w, mm.w, Lr.w);
+            un.x = fmaf(mm.x, Lr.x, fmaf(2.0f, c.x, -up.x));
+            un.y = fmaf(mm.y, Lr.y, fmaf(2.0f, c.y, -up.y));
+            un.z = fmaf(mm.z, Lr.z, fmaf(2.0f, c.z, -up.z));
+            un.w = fmaf(mm.w, Lr.w, fmaf(2.0f, c.w, -up.w));
             const int j = gj0 + r;
             float4 phn = make_float4(0.f, 0.f, 0.f, 0.f);
             bool any_pml = false;
             if (PML) {
-                const float4 ph = lds128(pu + 2 * P_TILE + pr);
+                const float4 ph = lds128(pph + pr);
                 phn = ph;
                 const int dyj = pml_depth(a.ny, a.nb, j);
                 const int dyp = pml_depth(a.ny, a.nb, j + 1), dym = pml_depth(a.ny, a.nb, j - 1);
@@ -357,13 +509,14 @@ struct StepCta {
                     const bool pt = (dxi | dyj | dzk) != 0;
                     any_pml |= pt;
                     const float edt = fmaf(a.ax, float(dxi * dxi), eyz);
-                    const float G = a.kx * float(dxp * dxp - dxm * dxm) * (w[5 + e] - w[3 + e]) +
-                                    gyk * f4get(gy[r], e) + gzk * (f4get(zp, e) - f4get(zm, e));
+                    float Gd = a.kx * float(dxp * dxp - dxm * dxm) * (w[5 + e] - w[3 + e]) +
+                               gyk * f4get(gy[r], e) + gzk * (f4get(zp, e) - f4get(zm, e));
+                    if constexpr (SCALED) Gd *= s_cur;
                     const float inv = __frcp_rn(1.0f + edt);
                     const float cc = f4get(c, e), pe = f4get(ph, e);
                     const float upml = ((2.0f - edt * edt) * cc - (1.0f - edt) * f4get(up, e) +
                                         f4get(mm, e) * (f4get(Lr, e) + pe)) * inv;
-                    const float ppml = (pe - G) * inv;
+                    const float ppml = (pe - Gd) * inv;
                     if (pt) {
                         f4set(un, e, upml);
                         f4set(phn, e, ppml);
@@ -377,18 +530,20 @@ struct StepCta {
             }
             if (store_ok && j < a.Ny) {
                 const long long off = off0 + (long long)r * a.sx;
+                if constexpr (SCALED) {
+                    vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(un.x), fabsf(un.y)),
+                                             fmaxf(fabsf(un.z), fabsf(un.w))));
+                    un = f4mul(inv_s_next, un);
+                }
+                T *uo = static_cast<T *>(a.u_out) + off;
+                uint32_t rnd = 0;
+                if constexpr (sizeof(T) == 2) rnd = hash_bits((uint32_t)off, (uint32_t)n);
                 if (gi + 3 < a.Nx) {
-#ifdef SGB_STORE_EVICT_FIRST
-                    const uint64_t pol = policy_evict_first();
-                    stg128_hint(a.u_out + off, un, pol);
-                    if (PML && any_pml) stg128_hint(a.phi + off, phn, pol);
-#else
-                    stg128(a.u_out + off, un);
+                    E::st(uo, un, rnd);
                     if (PML && any_pml) stg128(a.phi + off, phn);
-#endif
                 } else {
                     for (int e = 0; e < 4 && gi + e < a.Nx; ++e) {
-                        a.u_out[off + e] = f4get(un, e);
+                        E::put(uo + e, f4get(un, e), hash_bits(rnd, (uint32_t)e));
                         if (PML && any_pml) a.phi[off + e] = f4get(phn, e);
                     }
                 }
@@ -439,8 +594,27 @@ struct StepCta {
     }
 };
 
-template <class C>
-__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+// Power-of-two fp16 scale for a field bounded by B: B / scale < 2^14.
+__device__ __forceinline__ float pow2_scale_for(float B)
+{
+    if (!(B > 0.0f) || !isfinite(B)) return 1.0f;
+    return ldexpf(1.0f, ilogbf(B) + 1 - 14);
+}
+
+// Resident CTAs per SM asked of the compiler: 16-bit storage halves the u
+// ring's shared memory, leaving room for a third CTA if registers allow.
+template <class C, class T>
+constexpr int min_blocks()
+{
+#ifdef SGB_MINB16
+    return sizeof(T) == 2 ? SGB_MINB16 : C::MINB;
+#else
+    return C::MINB;
+#endif
+}
+
+template <class C, class T>
+__global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     fused_step_kernel(const __grid_constant__ StepArgs a,
                       const __grid_constant__ CUtensorMap tm_ucur,
                       const __grid_constant__ CUtensorMap tm_ucur_in,
@@ -448,10 +622,10 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
                       const __grid_constant__ CUtensorMap tm_m,
                       const __grid_constant__ CUtensorMap tm_phi)
 {
-    using S = StepCta<C>;
+    using S = StepCta<C, T>;
+    using G = Stage<C, T>;
     constexpr int TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
     constexpr int BX = C::BX, BY = C::BY;
-    constexpr int U_STAGE = C::U_STAGE, P_STAGE = C::P_STAGE;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S st;
@@ -461,9 +635,9 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     st.tm_uprev = &tm_uprev;
     st.tm_m = &tm_m;
     st.tm_phi = &tm_phi;
-    st.su = reinterpret_cast<float *>(smem_raw);
-    st.sp = st.su + NU * U_STAGE;
-    st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * P_STAGE);
+    st.su = smem_raw;
+    st.sp = smem_raw + NU * G::U_BYTES;
+    st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES);
     st.empty_u = st.full_u + NU;
     st.full_p = st.empty_u + NU;
     st.empty_p = st.full_p + NP;
@@ -488,14 +662,31 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     st.z0 = chunk * a.zc;
     st.z1 = min(st.z0 + a.zc, a.Nz);
     const int nit = st.z1 - st.z0;
-    st.n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
+    const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
+    st.n = n;
     st.aborted = false;
+    st.s_cur = st.s_prev = st.inv_s_next = 1.0f;
+    st.vmax = 0.0f;
+    if constexpr (S::SCALED) {
+        ScaleState *ss = a.scale;
+        st.s_cur = ss->s[n & 3];
+        st.s_prev = ss->s[(n - 1) & 3];
+        const float inj = a.sk >= 0 ? fabsf(*a.m_src * a.wavelet[n] * a.inv_vol) : 0.0f;
+        const float B = 4.0f * fmaxf(ss->mx[n & 3], ss->mx[(n - 1) & 3]) + inj;
+        const float s_next = pow2_scale_for(B);
+        st.inv_s_next = 1.0f / s_next;  // exact: a power of two
+        if (blockIdx.x == 0 && tid == 0) {
+            ss->s[(n + 1) & 3] = s_next;
+            ss->mx[(n + 2) & 3] = 0.0f;
+        }
+    }
 
     // Receivers of the previous step: u^n is read-only in this launch.
-    if (a.nrec > 0 && st.n >= 1) {
+    if (a.nrec > 0 && n >= 1) {
+        const T *uc = static_cast<const T *>(a.u_cur);
         for (int r = blockIdx.x * C::BLOCK + tid; r < a.nrec; r += gridDim.x * C::BLOCK) {
-            const float v = a.u_cur[a.rec_off[r]];
-            a.traces[(long long)(st.n - 1) * a.nrec + r] = v;
+            const float v = Elem<T>::get(uc + a.rec_off[r]) * st.s_cur;
+            a.traces[(long long)(n - 1) * a.nrec + r] = v;
             if (!isfinite(v)) atomicOr(a.err, DEV_ERR_NONFINITE);
         }
     }
@@ -527,7 +718,7 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
 
     const int txi = tid % C::TXT, tyi = tid / C::TXT;
     st.row0 = R + TY * tyi;
-    st.colu = C::HX + 4 * txi;
+    st.colu = G::HX + 4 * txi;
     st.gi = st.x0 + 4 * txi;
     st.gj0 = st.y0 + TY * tyi;
     st.prow = (TY * tyi) * BX + 4 * txi;
@@ -540,8 +731,7 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     for (int s = 0; s < 8; ++s) {
         st.wait(st.full_u + s, 0);
 #pragma unroll
-        for (int r = 0; r < TY; ++r)
-            q[r][s] = lds128(st.su + s * U_STAGE + st.own_off(st.z0 - 4 + s, r));
+        for (int r = 0; r < TY; ++r) q[r][s] = Elem<T>::ld(st.ustage(s) + st.own_off(st.z0 - 4 + s, r));
     }
     // planes z0-4 .. z0-1 (slots 0..3) are not needed again
     __syncwarp();
@@ -559,6 +749,13 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
         st.template segment<true>(q, 0, a0);
         st.template segment<false>(q, a0, a1);
         st.template segment<true>(q, a1, nit);
+    }
+
+    if constexpr (S::SCALED) {  // max |u^{n+1}| for the next step's scale
+        float v = st.vmax;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (st.lane == 0 && v > 0.0f) atomicMax(reinterpret_cast<int *>(&a.scale->mx[(n + 1) & 3]),
+                                                 __float_as_int(v));
     }
 }
 
