@@ -53,6 +53,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="skip the oracle CPU-baseline leg (profiling runs)")
     p.add_argument("--roofline-launches", type=int, default=100)
+    p.add_argument("--serve-requests", type=int, default=256,
+                   help="shot requests in the serving leg (0: skip)")
     p.add_argument("--oracle-steps", type=int, default=40,
                    help="time steps per oracle sample (CPU baseline / reference arm)")
     return p.parse_args()
@@ -158,6 +160,91 @@ def _time_oracle(w, vel, wav, src, rec, steps, nthreads):
     oracle.run_shot(g, vel, wav, steps, src, rec, nthreads=nthreads, want_state=False)
     ts = time.perf_counter() - t
     return max(ts - t0, 1e-9), ts, t0
+
+
+def _serving(a, seisgb, synth, single_gpts):
+    """Continuous-batching leg: Poisson arrivals at 0.8x the capacity implied by
+    the single-shot throughput; shots/s and latency percentiles (submit ->
+    traces on the host, measured by the server)."""
+    import threading
+
+    reqs = synth.serving_requests(a.serve_requests, seed=4)
+    work = []
+    for r in reqs:
+        vmax = float(r["velocity"].max())
+        g0 = seisgb.make_grid(r["nx"], r["ny"], r["nz"], r["nb"], r["h"], r["h"], r["h"], 1.0, vmax)
+        dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, vmax)))
+        g = seisgb.make_grid(r["nx"], r["ny"], r["nz"], r["nb"], r["h"], r["h"], r["h"], dt, vmax)
+        work.append((g, r, synth.ricker(r["nt"], dt, r["fp"])))
+    pts = [float(np.prod(r["velocity"].shape)) * r["nt"] for r in reqs]
+    # single-stream capacity of this mix: each grid size's throughput when it
+    # runs alone (run_shot, 300 steps), weighted by the mix's work
+    import torch
+    solo = {}
+    for key in sorted({r["velocity"].shape for r in reqs}):
+        g, r, wav = next(x for x in work if x[1]["velocity"].shape == key)
+        d_v = torch.from_numpy(r["velocity"]).cuda()
+        d_w = torch.from_numpy(wav[:300].copy()).cuda()
+        tr = torch.zeros((300, r["rec"].shape[0]), device="cuda")
+        seisgb.run_shot(g, d_v, d_w, 300, r["src"], r["rec"], tr)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        seisgb.run_shot(g, d_v, d_w, 300, r["src"], r["rec"], tr)
+        torch.cuda.synchronize()
+        solo[key] = float(np.prod(key)) * 300 / (time.perf_counter() - t) / 1e9
+    service = [float(np.prod(r["velocity"].shape)) * r["nt"] / (solo[r["velocity"].shape] * 1e9)
+               for r in reqs]
+    capacity = 1.0 / float(np.mean(service))  # shots/s, one shot at a time
+    rate = 0.8 * capacity
+    rng = np.random.default_rng(44)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    tickets = [None] * len(reqs)
+    with seisgb.Server(96 << 30, max_slots=16, steps_per_graph=16) as sv:
+        t0 = time.perf_counter()
+
+        def client():
+            for i, (g, r, wav) in enumerate(work):
+                d = arrivals[i] - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = sv.submit(g, r["velocity"], wav, r["nt"], r["src"], r["rec"])
+
+        th = threading.Thread(target=client)
+        th.start()
+        lat, queue = [], []
+        for i, (g, r, wav) in enumerate(work):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            rc, res, _ = sv.poll(tickets[i], r["nt"], r["rec"].shape[0], timeout_us=600_000_000)
+            lat.append(res.latency_ms)
+            queue.append(res.queue_ms)
+        th.join()
+        total = time.perf_counter() - t0
+        st = sv.stats()
+    lat = np.array(lat)
+    # overload: the first 64 requests submitted at once -> batched capacity
+    K = min(64, len(work))
+    with seisgb.Server(96 << 30, max_slots=16, steps_per_graph=16) as sv:
+        t1 = time.perf_counter()
+        tk = [sv.submit(g, r["velocity"], wav, r["nt"], r["src"], r["rec"]) for g, r, wav in work[:K]]
+        for t, (g, r, wav) in zip(tk, work[:K]):
+            sv.poll(t, r["nt"], r["rec"].shape[0], timeout_us=600_000_000)
+        t_over = time.perf_counter() - t1
+    overload = {"requests": K, "shots_per_s": K / t_over,
+                "gpts_aggregate": sum(pts[:K]) / t_over / 1e9,
+                "single_stream_shots_per_s": K / sum(service[:K])}
+    return {"requests": len(reqs), "shots_per_s": len(reqs) / total,
+            "gpts_aggregate": sum(pts) / total / 1e9, "offered_rate_per_s": rate,
+            "single_stream_capacity_per_s": capacity,
+            "solo_gpts": {"x".join(str(v) for v in k[::-1]): round(v, 1) for k, v in solo.items()},
+            "mean_solo_service_ms": float(np.mean(service)) * 1e3,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_queue_ms": float(np.mean(queue)), "wall_s": total,
+            "graph_replays": int(st.graph_replays), "step_launches": int(st.step_launches),
+            "overload": overload,
+            "config": "Poisson arrivals at 0.8x the single-stream capacity of this mix; grids 128^3, "
+                      "192x192x256, 256^3, 384x384x256 (PML 16); 500-2000 steps; seed 4; "
+                      "16 slots, 16 steps per graph"}
 
 
 def run_reference(a):
@@ -306,6 +393,8 @@ def main():
             "frac": alg16 / (pms / w.nt / 1e3) / 1e9 / peak,
             "error": "relative L2 vs the fp64 oracle: see the 256^3 x 1000-step precision test"}
 
+    serving = _serving(a, seisgb, synth, value) if a.serve_requests > 0 else None
+
     # end to end through the C ABI with pinned host buffers: velocity and wavelet
     # copied in, traces copied out, every step
     h_v = torch.from_numpy(vel).pin_memory()
@@ -345,6 +434,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "precision": precision,
+        "serving": serving,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle

@@ -147,6 +147,72 @@ int run_shot_noalloc(const sgb_grid *g, const float *velocity, const float *wave
                      const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
                      float *final_u, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of shot requests (no counterpart in the paper;
+ * every shot is Algorithm 1 on its own grid).  A server owns one GPU (the
+ * current device at serve_create), a stream and a scheduler thread.  Requests
+ * are admitted in FIFO order whenever a slot is free and the server's HBM
+ * budget can hold their footprint; all resident shots, whatever their grid
+ * sizes, advance together: each time step is one launch that covers the work
+ * units of every resident shot, and steps run in CUDA graphs of
+ * steps_per_graph launches.  Shots join and leave between graph replays.  A
+ * shot's results equal run_shot's for the same request.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* device memory the resident shots may hold */
+    int32_t max_slots;          /* shots resident at once, 1..64 */
+    int32_t steps_per_graph;    /* time steps per CUDA-graph replay, 1..256 */
+} sgb_serve_config;
+
+typedef struct {
+    sgb_grid grid;              /* storage must be SGB_FP32; dt within the CFL
+                                   limit of the model's maximum velocity */
+    const float *velocity;      /* host, Nz*Ny*Nx compact, copied at submit */
+    const float *wavelet;       /* host, nt samples, copied at submit */
+    int32_t nt;                 /* time steps, >= 1 */
+    int32_t src_ijk[3];         /* source, inside the inner region */
+    const int32_t *rec_ijk;     /* host, nrec*3, copied at submit */
+    int32_t nrec;               /* >= 1 */
+} sgb_shot_request;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;             /* SGB_OK or the error that ended the shot */
+    int32_t nt, nrec;
+    float *traces;              /* caller buffer of nt*nrec floats (or NULL);
+                                   filled when serve_poll returns SGB_OK */
+    double queue_ms;            /* submit -> admission */
+    double latency_ms;          /* submit -> traces on the host */
+} sgb_shot_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    int32_t resident, queued;
+    uint64_t graph_replays, step_launches;
+    uint64_t device_bytes;      /* bytes held by resident shots */
+} sgb_serve_stats;
+
+typedef struct sgb_server sgb_server;
+
+/* Device bytes a request holds while resident: four padded fp32 fields
+ * (u^n, u^{n-1}, phi, m), the velocity upload, wavelet, receiver table and
+ * traces.  Pure host arithmetic. */
+int serve_footprint(const sgb_grid *g, int32_t nt, int32_t nrec, uint64_t *bytes);
+/* Start a server on the current device.  OUT_OF_MEMORY / CUDA_ERROR on failure. */
+int serve_create(const sgb_serve_config *cfg, sgb_server **out);
+/* Queue a request (deep-copied; the caller's buffers may be reused at once).
+ * REJECTED if its footprint exceeds the whole budget, INVALID_ARG /
+ * UNSTABLE_DT on a bad request (checked before queueing). */
+int serve_submit(sgb_server *s, const sgb_shot_request *req, uint64_t *ticket);
+/* Result of a ticket.  SGB_OK: done, *out filled and traces copied (the ticket
+ * is then forgotten).  SGB_PENDING: not done and timeout_us == 0.
+ * SGB_ERR_TIMEOUT: not done within timeout_us (> 0).  INVALID_ARG: unknown. */
+int serve_poll(sgb_server *s, uint64_t ticket, sgb_shot_result *out, int32_t timeout_us);
+int serve_stats(sgb_server *s, sgb_serve_stats *out);
+/* Cancel queued requests, finish resident shots, stop the scheduler, free all
+ * device memory. */
+int serve_destroy(sgb_server *s);
+
 /* Layout conversion between compact (Nz, Ny, Nx) fp32 arrays and the padded
  * layout (device pointers; pack zeroes the halo).  Asynchronous on stream. */
 int sgb_pack(const sgb_grid *g, const float *compact, float *padded, void *stream);

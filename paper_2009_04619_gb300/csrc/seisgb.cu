@@ -933,3 +933,5 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
     if (dev_err & DEV_ERR_NONFINITE) return fail(SGB_ERR_NONFINITE, "a receiver sampled NaN/Inf");
     return SGB_OK;
 }
+
+#include "serve_impl.cuh"

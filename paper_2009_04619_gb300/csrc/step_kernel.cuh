@@ -613,14 +613,17 @@ constexpr int min_blocks()
 #endif
 }
 
+// The five tensor maps of one step: u^n with halo, u^n interior, u^{n-1}, m, phi.
+struct StepMapPtrs {
+    const CUtensorMap *ucur, *ucur_in, *uprev, *m, *phi;
+};
+
+// One work unit (tile x z-chunk, index `unit` of `units`) of step n.  With
+// sample_only, only the receivers of the previous step are sampled (the extra
+// launch after a shot's last step).
 template <class C, class T>
-__global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
-    fused_step_kernel(const __grid_constant__ StepArgs a,
-                      const __grid_constant__ CUtensorMap tm_ucur,
-                      const __grid_constant__ CUtensorMap tm_ucur_in,
-                      const __grid_constant__ CUtensorMap tm_uprev,
-                      const __grid_constant__ CUtensorMap tm_m,
-                      const __grid_constant__ CUtensorMap tm_phi)
+__device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &tm, int unit,
+                                          int units, int n, bool sample_only)
 {
     using S = StepCta<C, T>;
     using G = Stage<C, T>;
@@ -630,11 +633,11 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S st;
     st.pa = &a;
-    st.tm_ucur = &tm_ucur;
-    st.tm_ucur_in = &tm_ucur_in;
-    st.tm_uprev = &tm_uprev;
-    st.tm_m = &tm_m;
-    st.tm_phi = &tm_phi;
+    st.tm_ucur = tm.ucur;
+    st.tm_ucur_in = tm.ucur_in;
+    st.tm_uprev = tm.uprev;
+    st.tm_m = tm.m;
+    st.tm_phi = tm.phi;
     st.su = smem_raw;
     st.sp = smem_raw + NU * G::U_BYTES;
     st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES);
@@ -654,15 +657,14 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     // Work unit: chunk-major so that CTAs running together share z and their
     // x-y halos meet in L2.
     const int per_chunk = a.tiles_x * a.tiles_y;
-    const int chunk = blockIdx.x / per_chunk;
-    const int trem = blockIdx.x - chunk * per_chunk;
+    const int chunk = unit / per_chunk;
+    const int trem = unit - chunk * per_chunk;
     const int tyl = trem / a.tiles_x, txl = trem - tyl * a.tiles_x;
     st.x0 = txl * BX;
     st.y0 = tyl * BY;
     st.z0 = chunk * a.zc;
     st.z1 = min(st.z0 + a.zc, a.Nz);
     const int nit = st.z1 - st.z0;
-    const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     st.n = n;
     st.aborted = false;
     st.s_cur = st.s_prev = st.inv_s_next = 1.0f;
@@ -675,7 +677,7 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
         const float B = 4.0f * fmaxf(ss->mx[n & 3], ss->mx[(n - 1) & 3]) + inj;
         const float s_next = pow2_scale_for(B);
         st.inv_s_next = 1.0f / s_next;  // exact: a power of two
-        if (blockIdx.x == 0 && tid == 0) {
+        if (unit == 0 && tid == 0 && !sample_only) {
             ss->s[(n + 1) & 3] = s_next;
             ss->mx[(n + 2) & 3] = 0.0f;
         }
@@ -684,12 +686,14 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     // Receivers of the previous step: u^n is read-only in this launch.
     if (a.nrec > 0 && n >= 1) {
         const T *uc = static_cast<const T *>(a.u_cur);
-        for (int r = blockIdx.x * C::BLOCK + tid; r < a.nrec; r += gridDim.x * C::BLOCK) {
+        for (int r = unit * C::BLOCK + tid; r < a.nrec; r += units * C::BLOCK) {
             const float v = Elem<T>::get(uc + a.rec_off[r]) * st.s_cur;
             a.traces[(long long)(n - 1) * a.nrec + r] = v;
             if (!isfinite(v)) atomicOr(a.err, DEV_ERR_NONFINITE);
         }
     }
+
+    if (sample_only) return;
 
     const int xe = min(st.x0 + BX, a.Nx), ye = min(st.y0 + BY, a.Ny);
     st.xy_inner = st.x0 >= a.nb && xe <= a.nb + a.nx && st.y0 >= a.nb && ye <= a.nb + a.ny;
@@ -757,6 +761,21 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
         if (st.lane == 0 && v > 0.0f) atomicMax(reinterpret_cast<int *>(&a.scale->mx[(n + 1) & 3]),
                                                  __float_as_int(v));
     }
+}
+
+// One time step of one grid: one CTA per work unit.
+template <class C, class T>
+__global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
+    fused_step_kernel(const __grid_constant__ StepArgs a,
+                      const __grid_constant__ CUtensorMap tm_ucur,
+                      const __grid_constant__ CUtensorMap tm_ucur_in,
+                      const __grid_constant__ CUtensorMap tm_uprev,
+                      const __grid_constant__ CUtensorMap tm_m,
+                      const __grid_constant__ CUtensorMap tm_phi)
+{
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi};
+    const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
+    step_unit<C, T>(a, tm, blockIdx.x, gridDim.x, n, false);
 }
 
 }  // namespace sgb

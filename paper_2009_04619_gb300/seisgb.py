@@ -68,6 +68,30 @@ class Receivers(ctypes.Structure):
     _fields_ = [("nrec", ctypes.c_int32), ("ijk", ctypes.c_void_p), ("traces", ctypes.c_void_p)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("steps_per_graph", ctypes.c_int32)]
+
+
+class ShotRequest(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("velocity", ctypes.c_void_p), ("wavelet", ctypes.c_void_p),
+                ("nt", ctypes.c_int32), ("src_ijk", ctypes.c_int32 * 3),
+                ("rec_ijk", ctypes.c_void_p), ("nrec", ctypes.c_int32)]
+
+
+class ShotResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("nt", ctypes.c_int32),
+                ("nrec", ctypes.c_int32), ("traces", ctypes.c_void_p),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("resident", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("graph_replays", ctypes.c_uint64),
+                ("step_launches", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 
 # name -> (restype, argtypes); every symbol declared in include/seisgb.h
@@ -90,6 +114,15 @@ SIGNATURES = {
                                 ctypes.c_void_p]),
     "sgb_unpack": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p]),
+    "serve_footprint": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "serve_create": (ctypes.c_int, [ctypes.POINTER(ServeConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ShotRequest),
+                                    ctypes.POINTER(ctypes.c_uint64)]),
+    "serve_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ShotResult),
+                                  ctypes.c_int32]),
+    "serve_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServeStats)]),
+    "serve_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sgb_device_status": (ctypes.c_int, [ctypes.c_void_p]),
     "sgb_launch_count": (ctypes.c_int64, [ctypes.c_int]),
     "sgb_last_error": (ctypes.c_char_p, []),
@@ -223,3 +256,59 @@ def launch_count(reset: bool = False) -> int:
 
 def last_error() -> str:
     return lib().sgb_last_error().decode()
+
+
+def serve_footprint(g: Grid, nt: int, nrec: int) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().serve_footprint(ctypes.byref(g), int(nt), int(nrec), ctypes.byref(out)))
+    return out.value
+
+
+class Server:
+    """Continuous-batching shot server on the current device (the C API's
+    serve_create / serve_submit / serve_poll / serve_destroy)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, steps_per_graph: int = 16):
+        cfg = ServeConfig(int(hbm_budget_bytes), int(max_slots), int(steps_per_graph))
+        h = ctypes.c_void_p()
+        _check(lib().serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, g: Grid, velocity: np.ndarray, wavelet: np.ndarray, nt: int, src_ijk,
+               rec_ijk) -> int:
+        v = np.ascontiguousarray(velocity, dtype=np.float32)
+        w = np.ascontiguousarray(wavelet, dtype=np.float32)
+        r = np.ascontiguousarray(np.asarray(rec_ijk, dtype=np.int32).reshape(-1, 3))
+        req = ShotRequest(g, v.ctypes.data, w.ctypes.data, int(nt),
+                          (ctypes.c_int32 * 3)(*[int(x) for x in src_ijk]), r.ctypes.data,
+                          r.shape[0])
+        t = ctypes.c_uint64()
+        _check(lib().serve_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, nt: int, nrec: int, timeout_us: int = 0):
+        """(code, result, traces): code OK with traces [nt, nrec], PENDING or
+        ERR_TIMEOUT (traces None)."""
+        tr = np.zeros((nt, nrec), dtype=np.float32)
+        res = ShotResult(0, 0, 0, 0, tr.ctypes.data, 0.0, 0.0)
+        rc = lib().serve_poll(self.h, int(ticket), ctypes.byref(res), int(timeout_us))
+        if rc in (PENDING, ERR_TIMEOUT):
+            return rc, None, None
+        _check(rc)
+        return rc, res, tr
+
+    def stats(self) -> ServeStats:
+        out = ServeStats()
+        _check(lib().serve_stats(self.h, ctypes.byref(out)))
+        return out
+
+    def close(self):
+        if self.h:
+            _check(lib().serve_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -153,3 +153,33 @@ def scaled(w: Workload, n_inner: int, nb: int, nt: int, name: str | None = None)
     return Workload(name=name or f"{w.name}@{N}", nx=n_inner, ny=n_inner, nz=n_inner, nb=nb, h=w.h,
                     nt=nt, fp=w.fp, model=w.model, v_const=w.v_const, seed=w.seed, src=src,
                     rec_every=w.rec_every, cfl_fraction=w.cfl_fraction)
+
+
+# Serving workload: shot requests over four grid sizes (computed x, y, z; PML 16).
+SERVE_GRIDS = [(128, 128, 128), (192, 192, 256), (256, 256, 256), (384, 384, 256)]
+
+
+def serving_requests(n: int = 256, seed: int = 4, nb: int = 16, h: float = 10.0, fp: float = 10.0,
+                     nt_range=(500, 2000), models_per_grid: int = 8, rec_every: int = 8):
+    """Seeded shot requests: grid uniform over SERVE_GRIDS, nt uniform in
+    nt_range, a layered model (1500-4500 m/s, drawn from a pool of
+    models_per_grid seeded models per grid), source uniform over the inner
+    top surface 20 m deep, receivers on every rec_every-th inner surface point.
+    Returns a list of dicts (the velocity arrays are shared within a pool)."""
+    rng = np.random.default_rng(seed)
+    pool = {}
+    out = []
+    for i in range(n):
+        gx, gy, gz = SERVE_GRIDS[int(rng.integers(len(SERVE_GRIDS)))]
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        mseed = int(rng.integers(models_per_grid))
+        key = (gx, gy, gz, mseed)
+        if key not in pool:
+            pool[key] = layered_model((gz, gy, gx), seed=seed * 1000 + 17 * len(pool) + mseed,
+                                      perturb=0.0)
+        nx, ny, nz = gx - 2 * nb, gy - 2 * nb, gz - 2 * nb
+        src = (nb + int(rng.integers(nx)), nb + int(rng.integers(ny)), nb + 2)
+        out.append({"nx": nx, "ny": ny, "nz": nz, "nb": nb, "h": h, "nt": nt, "fp": fp,
+                    "velocity": pool[key], "src": src,
+                    "rec": surface_receivers(nx, ny, nb, rec_every)})
+    return out

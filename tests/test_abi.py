@@ -127,3 +127,23 @@ def test_run_shot_argument_checks_without_gpu(lib):
     rc = L.run_shot(ctypes.byref(g), v.ctypes.data, w.ctypes.data, -1, src.ctypes.data, None, 0,
                     None, None, None)
     assert rc == seisgb.ERR_INVALID_ARG
+
+
+def test_serve_footprint_arithmetic(lib):
+    """Four padded fp32 fields + velocity upload + wavelet + receiver table + traces."""
+    g = seisgb.make_grid(20, 24, 16, 6, 10, 10, 10, 1e-3, 3000)
+    L = seisgb.layout(g)
+    nt, nrec = 300, 17
+    Nz, Ny, Nx = g.shape
+    want = 4 * L.elems * 4 + Nz * Ny * Nx * 4 + nt * 4 + nrec * 8 + nt * nrec * 4
+    assert seisgb.serve_footprint(g, nt, nrec) == want
+    with pytest.raises(seisgb.SeisgbError):
+        seisgb.serve_footprint(g, 0, nrec)
+
+
+@pytest.mark.parametrize("budget,slots,steps", [(0, 4, 16), (1 << 30, 0, 16), (1 << 30, 65, 16),
+                                                (1 << 30, 4, 0), (1 << 30, 4, 257)])
+def test_serve_config_rejected_without_gpu(lib, budget, slots, steps):
+    cfg = seisgb.ServeConfig(budget, slots, steps)
+    h = ctypes.c_void_p()
+    assert seisgb.lib().serve_create(ctypes.byref(cfg), ctypes.byref(h)) == seisgb.ERR_INVALID_ARG
