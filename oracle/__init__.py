@@ -80,6 +80,9 @@ def lib():
         L.ora_run_shot.argtypes = [gp, fp, fp, ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, dp, dp,
                                    ctypes.c_int]
         L.ora_run_shot.restype = ctypes.c_int
+        L.ora_adjoint_shot.argtypes = [gp, fp, fp, ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, dp,
+                                       ctypes.c_int]
+        L.ora_adjoint_shot.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -235,3 +238,24 @@ def run_shot(g: Grid, velocity: np.ndarray, wavelet: np.ndarray, nt: int, src, r
     if rc != 0:
         raise RuntimeError("oracle run_shot failed")
     return {"traces": traces, "u": u, "u_prev": up, "phi": ph}
+
+
+def adjoint_shot(g: Grid, velocity: np.ndarray, wavelet: np.ndarray, nt: int, src, rec,
+                 observed: np.ndarray, nthreads: int = 0):
+    """Misfit J = 1/2 sum (d - obs)^2 of a shot and its gradient dJ/dv (compact
+    (Nz, Ny, Nx), float64) by the discrete adjoint; observed: [nt, nrec]."""
+    vel = np.ascontiguousarray(velocity, dtype=np.float32)
+    w = np.ascontiguousarray(wavelet, dtype=np.float32)
+    rec = np.ascontiguousarray(np.asarray(rec, dtype=np.int32).reshape(-1, 3))
+    obs = np.ascontiguousarray(observed, dtype=np.float64)
+    assert obs.shape == (nt, rec.shape[0])
+    s = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+    J = np.zeros(1)
+    grad = np.zeros(g.shape)
+    rc = lib().ora_adjoint_shot(ctypes.byref(g.c()), _ptr(vel, ctypes.c_float),
+                                _ptr(w, ctypes.c_float), nt, _ptr(s, ctypes.c_int),
+                                _ptr(rec, ctypes.c_int), rec.shape[0], _ptr(obs), _ptr(J),
+                                _ptr(grad), nthreads)
+    if rc != 0:
+        raise RuntimeError("oracle adjoint_shot failed")
+    return float(J[0]), grad

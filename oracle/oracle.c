@@ -377,3 +377,157 @@ int ora_run_shot(const ora_grid *g, const float *velocity, const float *wavelet,
     free(buf);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Gradient of the trace misfit with respect to the velocity model.
+ *
+ * The paper has no adjoint; this is the exact discrete adjoint of the step
+ * above (Eq. 2 with the PML reading), written in the scaled variable
+ * w = M lambda, where lambda is the Lagrange multiplier of u and M the
+ * coefficient of (L u + phi + f) in the update (m inside, m / (1 + e) in the
+ * PML).  Backward in time, k = nt .. 1, starting from zero:
+ *   psi(x)  = sum_a [c_a nu(x + e_a) - c_a nu(x - e_a)] / (2 h_a),
+ *             c_a = dt (d eta / d x_a) / (1 + e) at PML points, 0 elsewhere
+ *             (the transpose of phi's grad(eta).grad(u) coupling);
+ *   w^k     = 2 w^{k+1} - w^{k+2} + m (L w^{k+1} + psi + K^T r^{k-1})   inside,
+ *             [(2 - e^2) w^{k+1} - (1 - e) w^{k+2} + m (...)] / (1 + e)   in the PML;
+ *   nu^k    = nu^{k+1} / (1 + e) + w^{k+1} at PML points (0 elsewhere);
+ *   dJ/dm  += w^k g^{k-1} / m,  g^n = L u^n + phi^n + f^n (forward);
+ * with r^n = d^n - obs^n the trace residual of J = 1/2 sum (d - obs)^2.
+ * Finally dJ/dv = dJ/dm * 2 v dt^2 (dt held fixed).  Plain: the forward
+ * history of g is kept whole (small grids only).
+ * ------------------------------------------------------------------------ */
+int ora_adjoint_shot(const ora_grid *g, const float *velocity, const float *wavelet, int nt,
+                     const int *src_ijk, const int *rec_ijk, int nrec, const double *observed,
+                     double *misfit, double *grad_v, int nthreads)
+{
+    int Nx = ext_x(g), Ny = ext_y(g), Nz = ext_z(g);
+    if (Nx <= 0 || Ny <= 0 || Nz <= 0 || nt < 1) return -1;
+    size_t n = ora_field_len(g);
+    long sx = Nx + 2 * R, sxy = sx * (Ny + 2 * R);
+    const long st3[3] = {1, sx, sxy};
+    const double hh[3] = {g->dx, g->dy, g->dz};
+    double *m = calloc(n, sizeof(double)), *eta = calloc(n, sizeof(double));
+    double *ua = calloc(n, sizeof(double)), *ub = calloc(n, sizeof(double)), *uc = calloc(n, sizeof(double));
+    double *pa = calloc(n, sizeof(double)), *pb = calloc(n, sizeof(double));
+    double *lap = calloc(n, sizeof(double));
+    double *gacc = calloc(n * (size_t)nt, sizeof(double));
+    double *traces = calloc((size_t)nt * (nrec > 0 ? nrec : 1), sizeof(double));
+    double *w1 = calloc(n, sizeof(double)), *w2 = calloc(n, sizeof(double)), *wk = calloc(n, sizeof(double));
+    double *nu = calloc(n, sizeof(double)), *nun = calloc(n, sizeof(double)), *psi = calloc(n, sizeof(double));
+    double *gm = calloc(n, sizeof(double)), *wl = calloc(n, sizeof(double));
+    if (!m || !eta || !ua || !ub || !uc || !pa || !pb || !lap || !gacc || !traces || !w1 || !w2 ||
+        !wk || !nu || !nun || !psi || !gm || !wl)
+        return -1;
+    double dt = g->dt;
+    for (int k = 0; k < Nz; ++k)
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                double v = (double)velocity[((size_t)k * Ny + j) * Nx + i];
+                m[ora_index(g, i, j, k)] = v * v * dt * dt;
+            }
+    ora_eta(g, eta);
+    double inv_vol = 1.0 / (g->dx * g->dy * g->dz);
+    long ps = src_ijk ? ora_index(g, src_ijk[0], src_ijk[1], src_ijk[2]) : -1;
+    /* forward, keeping g^n = L u^n + phi^n + f^n */
+    double *u_prev = ua, *u_cur = ub, *u_next = uc, *phi = pa, *phi_next = pb;
+    for (int step = 0; step < nt; ++step) {
+        ora_laplacian(g, u_cur, lap, nthreads);
+        double *gn = gacc + (size_t)step * n;
+        for (int k = 0; k < Nz; ++k)
+            for (int j = 0; j < Ny; ++j)
+                for (int i = 0; i < Nx; ++i) {
+                    long p = ora_index(g, i, j, k);
+                    gn[p] = lap[p] + (ora_is_pml(g, i, j, k) ? phi[p] : 0.0);
+                }
+        if (ps >= 0) gn[ps] += (double)wavelet[step] * inv_vol;
+        ora_step(g, m, eta, u_prev, u_cur, phi, u_next, phi_next, nthreads);
+        if (ps >= 0) u_next[ps] += m[ps] * (double)wavelet[step] * inv_vol;
+        for (int r = 0; r < nrec; ++r)
+            traces[(size_t)step * nrec + r] =
+                u_next[ora_index(g, rec_ijk[3 * r], rec_ijk[3 * r + 1], rec_ijk[3 * r + 2])];
+        double *t = u_prev;
+        u_prev = u_cur;
+        u_cur = u_next;
+        u_next = t;
+        t = phi;
+        phi = phi_next;
+        phi_next = t;
+    }
+    double J = 0.0;
+    for (size_t q = 0; q < (size_t)nt * nrec; ++q) {
+        double d = traces[q] - observed[q];
+        J += 0.5 * d * d;
+    }
+    *misfit = J;
+    /* backward */
+    for (int kk = nt; kk >= 1; --kk) {
+        /* psi from nu^{k+1}; nu^k */
+        for (int k = 0; k < Nz; ++k)
+            for (int j = 0; j < Ny; ++j)
+                for (int i = 0; i < Nx; ++i) {
+                    long p = ora_index(g, i, j, k);
+                    int c[3] = {i, j, k};
+                    double s = 0.0;
+                    for (int ax = 0; ax < 3; ++ax)
+                        for (int sg = -1; sg <= 1; sg += 2) {
+                            int d[3] = {c[0], c[1], c[2]};
+                            d[ax] += sg;
+                            if (d[0] < 0 || d[0] >= Nx || d[1] < 0 || d[1] >= Ny || d[2] < 0 ||
+                                d[2] >= Nz || !ora_is_pml(g, d[0], d[1], d[2]))
+                                continue;
+                            long q = p + sg * st3[ax];
+                            double e = eta[q] * dt;
+                            double ca = dt * (eta[q + st3[ax]] - eta[q - st3[ax]]) / (2.0 * hh[ax]) /
+                                        (1.0 + e);
+                            s += sg * ca * nu[q] / (2.0 * hh[ax]);
+                        }
+                    psi[p] = s;
+                    if (ora_is_pml(g, i, j, k)) {
+                        double e = eta[p] * dt;
+                        nun[p] = nu[p] / (1.0 + e) + w1[p];
+                    } else {
+                        nun[p] = 0.0;
+                    }
+                }
+        ora_laplacian(g, w1, wl, nthreads);
+        for (int k = 0; k < Nz; ++k)
+            for (int j = 0; j < Ny; ++j)
+                for (int i = 0; i < Nx; ++i) {
+                    long p = ora_index(g, i, j, k);
+                    double a = wl[p] + psi[p];
+                    if (!ora_is_pml(g, i, j, k)) {
+                        wk[p] = 2.0 * w1[p] - w2[p] + m[p] * a;
+                    } else {
+                        double e = eta[p] * dt;
+                        wk[p] = ((2.0 - e * e) * w1[p] - (1.0 - e) * w2[p] + m[p] * a) / (1.0 + e);
+                    }
+                }
+        /* K^T r^{k-1}: the residual enters at the receivers, scaled by M = m there */
+        for (int r = 0; r < nrec; ++r) {
+            long p = ora_index(g, rec_ijk[3 * r], rec_ijk[3 * r + 1], rec_ijk[3 * r + 2]);
+            double res = traces[(size_t)(kk - 1) * nrec + r] - observed[(size_t)(kk - 1) * nrec + r];
+            wk[p] += m[p] * res;
+        }
+        const double *gk = gacc + (size_t)(kk - 1) * n;
+        for (size_t q = 0; q < n; ++q)
+            if (m[q] > 0.0) gm[q] += wk[q] * gk[q] / m[q];
+        double *t = w2;
+        w2 = w1;
+        w1 = wk;
+        wk = t;
+        t = nu;
+        nu = nun;
+        nun = t;
+    }
+    for (int k = 0; k < Nz; ++k)
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                long p = ora_index(g, i, j, k);
+                double v = (double)velocity[((size_t)k * Ny + j) * Nx + i];
+                grad_v[((size_t)k * Ny + j) * Nx + i] = gm[p] * 2.0 * v * dt * dt;
+            }
+    free(m); free(eta); free(ua); free(ub); free(uc); free(pa); free(pb); free(lap); free(gacc);
+    free(traces); free(w1); free(w2); free(wk); free(nu); free(nun); free(psi); free(gm); free(wl);
+    return 0;
+}

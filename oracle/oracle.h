@@ -66,6 +66,10 @@ int ora_run_shot(const ora_grid *g, const float *velocity, const float *wavelet,
                  const int *src_ijk, const int *rec_ijk, int nrec, double *traces,
                  double *u_final, double *u_prev_final, double *phi_final, int nthreads);
 
+int ora_adjoint_shot(const ora_grid *g, const float *velocity, const float *wavelet, int nt,
+                     const int *src_ijk, const int *rec_ijk, int nrec, const double *observed,
+                     double *misfit, double *grad_v, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif
