@@ -124,6 +124,26 @@ int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int
              const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
              float *final_u, void *stream);
 
+/* Trace misfit J = 1/2 sum_{n,r} (d^n_r - observed^n_r)^2 of a shot (d as in
+ * run_shot) and its gradient dJ/dv with respect to the velocity model, by the
+ * exact discrete adjoint of the fused step including the PML and the source
+ * (the paper has no adjoint; the derivation is in the oracle and the design
+ * notes).  The forward run keeps (u^n, u^{n-1}, phi^n) every ckpt_every steps
+ * (0: 100); the backward sweep recomputes each segment's forward steps and
+ * runs the adjoint steps over it.  The misfit sum and the time accumulation of
+ * the gradient are fp64; everything else fp32 (SGB_FP32 storage only).
+ *   velocity  Nz*Ny*Nx fp32 compact, host or device
+ *   wavelet   nt fp32, host or device;  src_ijk, rec_ijk: host
+ *   observed  nt*nrec fp32 (same layout as run_shot's traces), host or device
+ *   misfit_out     host double
+ *   grad_velocity  Nz*Ny*Nx fp64 compact, host or device
+ * Scratch: 9 padded fields, ceil(nt / ckpt_every) x 3 checkpoint fields and
+ * ckpt_every recomputation fields, from the library pool.  Synchronous. */
+int adjoint_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
+                 const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec,
+                 const float *observed, int32_t ckpt_every, double *misfit_out,
+                 double *grad_velocity, void *stream);
+
 /* Allocation-free variant of run_shot (the paper has no counterpart).  For
  * callers that cannot allocate device memory once running -- e.g. a serving
  * process whose device memory is all held by another allocator's pool, or a

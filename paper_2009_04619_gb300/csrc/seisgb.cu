@@ -935,3 +935,4 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
 }
 
 #include "serve_impl.cuh"
+#include "adjoint.cuh"

@@ -64,6 +64,11 @@ constexpr int HALO = 4;       // zero points before y = 0, z = 0 and after every
 
 enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_RANGE = 4 };
 
+// Kernel modes: the forward step; the forward step that also stores its
+// acceleration term g^n = L u^n + phi^n + f^n (recomputation for the adjoint);
+// the adjoint step (see adjoint notes below).
+enum : int { MODE_FWD = 0, MODE_FWD_ACC = 1, MODE_ADJ = 2 };
+
 // Scale state of a 16-bit wavefield pair (device memory): s[k & 3] is the
 // scale of u^k (stored value = u^k / s), mx[k & 3] is max |u^k|.
 struct ScaleState {
@@ -93,6 +98,8 @@ struct StepArgs {
     const long long *rec_off;
     float *traces;
     ScaleState *scale;     // fp16 storage only
+    float *acc_out;        // MODE_FWD_ACC: g = L u^n + phi^n + f^n (padded fp32)
+    double *grad_m;        // MODE_ADJ: dJ/dm accumulated in fp64 (padded)
     int *err;              // device error word
     int tiles_x, tiles_y, zc;
 };
@@ -233,14 +240,14 @@ struct TileCfg {
 };
 
 // Shared-memory geometry of a configuration for storage type T (bytes).
-template <class C, class T>
+template <class C, class T, int MODE = MODE_FWD>
 struct Stage {
     static constexpr int HX = Elem<T>::HX;         // x margin of the u^n box
     static constexpr int SW = C::BX + 2 * HX;      // u^n box width (elements)
     static constexpr int U_BYTES = align128(SW * C::SH * (int)sizeof(T));
     static constexpr int UP_BYTES = align128(C::P_TILE * (int)sizeof(T));
-    static constexpr int F_BYTES = C::P_TILE * 4;  // one fp32 tile (m or phi)
-    static constexpr int P_BYTES = UP_BYTES + 2 * F_BYTES;
+    static constexpr int F_BYTES = C::P_TILE * 4;  // one fp32 tile (m, phi / psi, g)
+    static constexpr int P_BYTES = UP_BYTES + (MODE == MODE_ADJ ? 3 : 2) * F_BYTES;
     static constexpr size_t SMEM_BYTES = size_t(C::NU) * U_BYTES + size_t(C::NP) * P_BYTES +
                                          size_t(C::NU + C::NP) * 16 +
                                          size_t(C::NU + C::NP + 1) * 4;
@@ -302,10 +309,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Per-thread state of one fused-step work unit (a tile x a z-chunk).
-template <class C, class T>
+template <class C, class T, int MODE = MODE_FWD>
 struct StepCta {
     using E = Elem<T>;
-    using G = Stage<C, T>;
+    using G = Stage<C, T, MODE>;
+    // the adjoint's PML-path band is one point wider: inner points next to the
+    // PML receive psi
+    static constexpr int BAND = MODE == MODE_ADJ ? 1 : 0;
     static constexpr bool SCALED = E::SCALED;
     static constexpr int TXT = C::TXT, TY = C::TY, NU = C::NU, NP = C::NP;
     static constexpr int THREADS = C::THREADS, QN = C::QN, U = C::U, WARPS = C::WARPS;
@@ -314,7 +324,7 @@ struct StepCta {
     static constexpr uint64_t WAIT_NS = 2000000000ull;
 
     const StepArgs *pa;  // the kernel argument, in the constant parameter space
-    const CUtensorMap *tm_ucur, *tm_ucur_in, *tm_uprev, *tm_m, *tm_phi;
+    const CUtensorMap *tm_ucur, *tm_ucur_in, *tm_uprev, *tm_m, *tm_phi, *tm_acc;
     unsigned char *su, *sp;  // u ring, (u^{n-1}, m, phi) ring
     uint64_t *full_u, *empty_u, *full_p, *empty_p;
     int *lastf_u, *lastf_p, *s_abort;
@@ -326,7 +336,7 @@ struct StepCta {
 
     __device__ __forceinline__ bool plane_pml(int k) const
     {
-        return !xy_inner || k < pa->nb || k >= pa->nb + pa->nz;
+        return !xy_inner || k < pa->nb + BAND || k >= pa->nb + pa->nz - BAND;
     }
 
     __device__ __forceinline__ void wait(uint64_t *bar, uint32_t parity)
@@ -373,12 +383,15 @@ struct StepCta {
         if (f > 0) wait(empty_p + s, (f - 1) & 1);
         lastf_p[s] = f;
         const bool pml = plane_pml(k);
-        mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + (pml ? 2 : 1) * G::F_BYTES);
+        const int ntiles = (pml ? 2 : 1) + (MODE == MODE_ADJ ? 1 : 0);
+        mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + ntiles * G::F_BYTES);
         unsigned char *d = sp + s * G::P_BYTES;
         const uint64_t pol = policy_evict_first();
         tma_load_3d_hint(d, tm_uprev, full_p + s, x0, y0, k, pol);
         tma_load_3d_hint(d + G::UP_BYTES, tm_m, full_p + s, x0, y0, k, pol);
         if (pml) tma_load_3d_hint(d + G::UP_BYTES + G::F_BYTES, tm_phi, full_p + s, x0, y0, k, pol);
+        if constexpr (MODE == MODE_ADJ)  // g^{k-1} of the forward recomputation, plane k
+            tma_load_3d_hint(d + G::UP_BYTES + 2 * G::F_BYTES, tm_acc, full_p + s, x0, y0, k, pol);
     }
 
     // Producer lane: every plane of u^n (z0-4 .. z1+3) and every (u^{n-1}, m,
@@ -423,6 +436,7 @@ struct StepCta {
         const T *pup = reinterpret_cast<const T *>(pu);
         const float *pm = reinterpret_cast<const float *>(pu + G::UP_BYTES);
         const float *pph = reinterpret_cast<const float *>(pu + G::UP_BYTES + G::F_BYTES);
+        const float *pg = reinterpret_cast<const float *>(pu + G::UP_BYTES + 2 * G::F_BYTES);
 
         // 25-point Laplacian (Eq. 3): centre and z part from the queue
         float4 L[TY], gy[TY];
@@ -493,8 +507,10 @@ struct StepCta {
             const int j = gj0 + r;
             float4 phn = make_float4(0.f, 0.f, 0.f, 0.f);
             bool any_pml = false;
+            int ptmask = 0;
+            float4 ph = make_float4(0.f, 0.f, 0.f, 0.f);
             if (PML) {
-                const float4 ph = lds128(pph + pr);
+                ph = lds128(pph + pr);
                 phn = ph;
                 const int dyj = pml_depth(a.ny, a.nb, j);
                 const int dyp = pml_depth(a.ny, a.nb, j + 1), dym = pml_depth(a.ny, a.nb, j - 1);
@@ -517,16 +533,31 @@ struct StepCta {
                     const float upml = ((2.0f - edt * edt) * cc - (1.0f - edt) * f4get(up, e) +
                                         f4get(mm, e) * (f4get(Lr, e) + pe)) * inv;
                     const float ppml = (pe - Gd) * inv;
-                    if (pt) {
+                    ptmask |= int(pt) << e;
+                    if constexpr (MODE == MODE_ADJ) {
+                        // adjoint: the phi slot holds psi, which also reaches the
+                        // inner points next to the PML; no phi update here
+                        f4set(un, e, pt ? upml
+                                        : fmaf(f4get(mm, e), f4get(Lr, e) + pe,
+                                               fmaf(2.0f, cc, -f4get(up, e))));
+                    } else if (pt) {
                         f4set(un, e, upml);
                         f4set(phn, e, ppml);
                     }
                 }
             }
+            float4 acc4 = Lr;  // MODE_FWD_ACC: g = L u^n + phi^n + f^n
+            if constexpr (MODE == MODE_FWD_ACC) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if ((ptmask >> e) & 1) f4set(acc4, e, f4get(acc4, e) + f4get(ph, e));
+            }
             // point source (Eq. 2 right-hand side), added by the owning thread
-            if (k == a.sk && j == a.sj && a.si >= gi && a.si < gi + 4) {
+            if (MODE != MODE_ADJ && k == a.sk && j == a.sj && a.si >= gi && a.si < gi + 4) {
                 const int e = a.si - gi;
-                f4set(un, e, f4get(un, e) + f4get(mm, e) * a.wavelet[n] * a.inv_vol);
+                const float f = a.wavelet[n] * a.inv_vol;
+                f4set(un, e, f4get(un, e) + f4get(mm, e) * f);
+                if constexpr (MODE == MODE_FWD_ACC) f4set(acc4, e, f4get(acc4, e) + f);
             }
             if (store_ok && j < a.Ny) {
                 const long long off = off0 + (long long)r * a.sx;
@@ -538,14 +569,24 @@ struct StepCta {
                 T *uo = static_cast<T *>(a.u_out) + off;
                 uint32_t rnd = 0;
                 if constexpr (sizeof(T) == 2) rnd = hash_bits((uint32_t)off, (uint32_t)n);
+                const bool wphi = MODE != MODE_ADJ && PML && any_pml;
                 if (gi + 3 < a.Nx) {
                     E::st(uo, un, rnd);
-                    if (PML && any_pml) stg128(a.phi + off, phn);
+                    if (wphi) stg128(a.phi + off, phn);
+                    if constexpr (MODE == MODE_FWD_ACC) stg128(a.acc_out + off, acc4);
                 } else {
                     for (int e = 0; e < 4 && gi + e < a.Nx; ++e) {
                         E::put(uo + e, f4get(un, e), hash_bits(rnd, (uint32_t)e));
-                        if (PML && any_pml) a.phi[off + e] = f4get(phn, e);
+                        if (wphi) a.phi[off + e] = f4get(phn, e);
+                        if constexpr (MODE == MODE_FWD_ACC) a.acc_out[off + e] = f4get(acc4, e);
                     }
+                }
+                if constexpr (MODE == MODE_ADJ) {
+                    // dJ/dm += w^k g^{k-1} / m, accumulated in fp64
+                    const float4 gk = lds128(pg + pr);
+                    for (int e = 0; e < 4 && gi + e < a.Nx; ++e)
+                        a.grad_m[off + e] +=
+                            (double)f4get(un, e) * (double)f4get(gk, e) / (double)f4get(mm, e);
                 }
             }
         }
@@ -616,17 +657,19 @@ constexpr int min_blocks()
 // The five tensor maps of one step: u^n with halo, u^n interior, u^{n-1}, m, phi.
 struct StepMapPtrs {
     const CUtensorMap *ucur, *ucur_in, *uprev, *m, *phi;
+    const CUtensorMap *acc;  // MODE_ADJ: g^{k-1}
 };
 
 // One work unit (tile x z-chunk, index `unit` of `units`) of step n.  With
 // sample_only, only the receivers of the previous step are sampled (the extra
 // launch after a shot's last step).
-template <class C, class T>
+template <class C, class T, int MODE = MODE_FWD>
 __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &tm, int unit,
                                           int units, int n, bool sample_only)
 {
-    using S = StepCta<C, T>;
-    using G = Stage<C, T>;
+    using S = StepCta<C, T, MODE>;
+    using G = Stage<C, T, MODE>;
+    static_assert(MODE == MODE_FWD || sizeof(T) == 4, "the adjoint runs in fp32");
     constexpr int TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
     constexpr int BX = C::BX, BY = C::BY;
 
@@ -638,6 +681,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     st.tm_uprev = tm.uprev;
     st.tm_m = tm.m;
     st.tm_phi = tm.phi;
+    st.tm_acc = tm.acc;
     st.su = smem_raw;
     st.sp = smem_raw + NU * G::U_BYTES;
     st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES);
@@ -696,7 +740,8 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     if (sample_only) return;
 
     const int xe = min(st.x0 + BX, a.Nx), ye = min(st.y0 + BY, a.Ny);
-    st.xy_inner = st.x0 >= a.nb && xe <= a.nb + a.nx && st.y0 >= a.nb && ye <= a.nb + a.ny;
+    st.xy_inner = st.x0 >= a.nb + S::BAND && xe <= a.nb + a.nx - S::BAND &&
+                  st.y0 >= a.nb + S::BAND && ye <= a.nb + a.ny - S::BAND;
 
     if (tid == THREADS) {
         *st.s_abort = 0;
@@ -748,8 +793,8 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     if (!st.xy_inner) {
         st.template segment<true>(q, 0, nit);
     } else {
-        const int a0 = min(max(a.nb - st.z0, 0), nit);
-        const int a1 = min(max(a.nb + a.nz - st.z0, a0), nit);
+        const int a0 = min(max(a.nb + S::BAND - st.z0, 0), nit);
+        const int a1 = min(max(a.nb + a.nz - S::BAND - st.z0, a0), nit);
         st.template segment<true>(q, 0, a0);
         st.template segment<false>(q, a0, a1);
         st.template segment<true>(q, a1, nit);
@@ -773,9 +818,39 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
                       const __grid_constant__ CUtensorMap tm_m,
                       const __grid_constant__ CUtensorMap tm_phi)
 {
-    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi};
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     step_unit<C, T>(a, tm, blockIdx.x, gridDim.x, n, false);
+}
+
+// Forward step that also stores g^n = L u^n + phi^n + f^n (adjoint recomputation).
+template <class C>
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+    fwd_acc_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tm_ucur,
+                   const __grid_constant__ CUtensorMap tm_ucur_in,
+                   const __grid_constant__ CUtensorMap tm_uprev,
+                   const __grid_constant__ CUtensorMap tm_m,
+                   const __grid_constant__ CUtensorMap tm_phi)
+{
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr};
+    step_unit<C, float, MODE_FWD_ACC>(a, tm, blockIdx.x, gridDim.x, a.step_add, false);
+}
+
+// Adjoint step k (see the adjoint notes in adjoint.cuh): reads w^{k+1} through
+// the u^n maps, w^{k+2} through the u^{n-1} map (overwritten with w^k), psi
+// through the phi map and g^{k-1} through the acc map.
+template <class C>
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+    adjoint_step_kernel(const __grid_constant__ StepArgs a,
+                        const __grid_constant__ CUtensorMap tm_ucur,
+                        const __grid_constant__ CUtensorMap tm_ucur_in,
+                        const __grid_constant__ CUtensorMap tm_uprev,
+                        const __grid_constant__ CUtensorMap tm_m,
+                        const __grid_constant__ CUtensorMap tm_psi,
+                        const __grid_constant__ CUtensorMap tm_acc)
+{
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_psi, &tm_acc};
+    step_unit<C, float, MODE_ADJ>(a, tm, blockIdx.x, gridDim.x, a.step_add, false);
 }
 
 }  // namespace sgb

@@ -106,6 +106,11 @@ SIGNATURES = {
     "run_shot": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "adjoint_shot": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "run_shot_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -220,6 +225,21 @@ def run_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, traces, fina
                           None if s is None else s.ctypes.data,
                           r.ctypes.data if nrec else None, nrec,
                           _ptr(traces) if nrec else None, _ptr(final_u), _stream(stream)))
+
+
+def adjoint_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, observed, grad_velocity,
+                 ckpt_every: int = 0, stream=None) -> float:
+    """Trace misfit J = 1/2 sum (d - observed)^2 and, into grad_velocity (fp64,
+    the velocity's shape, host or device), dJ/dv by the discrete adjoint with
+    checkpoints every ckpt_every steps (0: 100).  Returns J."""
+    s = np.ascontiguousarray(np.asarray(src_ijk, dtype=np.int32))
+    r = np.ascontiguousarray(np.asarray(rec_ijk, dtype=np.int32).reshape(-1, 3))
+    J = ctypes.c_double()
+    _check(lib().adjoint_shot(ctypes.byref(g), _ptr(velocity), _ptr(wavelet), int(nt),
+                              s.ctypes.data, r.ctypes.data, r.shape[0], _ptr(observed),
+                              int(ckpt_every), ctypes.byref(J), _ptr(grad_velocity),
+                              _stream(stream)))
+    return J.value
 
 
 def run_shot_noalloc(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, traces,
