@@ -55,6 +55,8 @@ def _args():
     p.add_argument("--roofline-launches", type=int, default=100)
     p.add_argument("--serve-requests", type=int, default=256,
                    help="shot requests in the serving leg (0: skip)")
+    p.add_argument("--grad-shots", type=int, default=16,
+                   help="shots of the adjoint-gradient leg (0: skip)")
     p.add_argument("--oracle-steps", type=int, default=40,
                    help="time steps per oracle sample (CPU baseline / reference arm)")
     return p.parse_args()
@@ -247,6 +249,80 @@ def _serving(a, seisgb, synth, single_gpts):
                       "16 slots, 16 steps per graph"}
 
 
+def _gradient_alg_bytes(w, nt, ckpt, fold=32):
+    """Compulsory HBM bytes of one gradient shot: the forward steps (16 B per
+    point, +8 B of phi on the PML), the checkpoint saves and restores (3 fields
+    read + written each), the recomputed steps (+4 B: g^n written), the adjoint
+    steps (w^{k+1}, w^{k+2}, m, g^{k-1}, S read; w^k, S written: 28 B, +8 B of
+    mu on the PML) and the fp64 folds of S (24 B per point every `fold` steps)."""
+    N = w.points
+    P = N - w.nx * w.ny * w.nz
+    segs = -(-nt // ckpt)
+    return (nt * ((16 + 20 + 28) * N + 24 * P) + 2 * segs * 24 * N
+            + -(-nt // fold) * 24 * N)
+
+
+def _gradient(a, seisgb, synth, peak):
+    """Adjoint-gradient leg: 16 shots of the 256^3 / 2000-step workload, misfit
+    against traces of the unperturbed model, gradients summed over the shots
+    (fp64); shots/s, forward-equivalent Gpt/s and the whole computation's
+    algorithmic bytes per second against the HBM peak."""
+    import torch
+    w = synth.GRADIENT
+    v, v_obs = synth.gradient_models(w)
+    vmax = float(max(v.max(), v_obs.max()))
+    g0 = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, 1.0, vmax)
+    dt = float(np.float32(w.cfl_fraction * seisgb.cfl_dt(g0, vmax)))
+    g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax)
+    nt, C = w.nt, w.extra["ckpt_every"]
+    wav = synth.ricker(nt, dt, w.fp)
+    rec = w.receivers()
+    shots = synth.shot_grid(w)[:a.grad_shots]
+    d_v = torch.from_numpy(v).cuda()
+    d_vo = torch.from_numpy(v_obs).cuda()
+    d_w = torch.from_numpy(wav).cuda()
+    obs = []
+    for src in shots:
+        o = torch.zeros((nt, rec.shape[0]), dtype=torch.float32, device="cuda")
+        seisgb.run_shot(g, d_vo, d_w, nt, src, rec, o)
+        obs.append(o)
+    grad = torch.zeros(v.shape, dtype=torch.float64, device="cuda")
+    total = torch.zeros_like(grad)
+    seisgb.adjoint_shot(g, d_v, d_w, nt, shots[0], rec, obs[0], grad, ckpt_every=C)  # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    J = 0.0
+    e0.record(stream)
+    for src, o in zip(shots, obs):
+        J += seisgb.adjoint_shot(g, d_v, d_w, nt, src, rec, o, grad, ckpt_every=C)
+        total += grad
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    tr = torch.zeros((nt, rec.shape[0]), dtype=torch.float32, device="cuda")
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for src in shots[:4]:
+        seisgb.run_shot(g, d_v, d_w, nt, src, rec, tr)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t_fwd = f0.elapsed_time(f1) / 1e3 / min(4, len(shots))
+    ns = len(shots)
+    alg = _gradient_alg_bytes(w, nt, C)
+    gbs = alg * ns / t / 1e9
+    return {"workload": w.name, "grid": list(w.shape), "nb": w.nb, "nt": nt, "shots": ns,
+            "ckpt_every": C, "nrec": int(rec.shape[0]),
+            "shots_per_s": ns / t, "ms_per_shot": t / ns * 1e3,
+            "gpts_forward_equivalent": w.points * nt * ns / t / 1e9,
+            "forward_ms_per_shot": t_fwd * 1e3, "ratio_to_forward": t / ns / t_fwd,
+            "alg_bytes_per_shot": alg, "achieved_gbs": gbs, "frac": gbs / peak,
+            "misfit": J, "grad_l2": float(total.norm()),
+            "grad_finite": bool(torch.isfinite(total).all()),
+            "accuracy": "gradient vs the fp64 oracle adjoint (32^3, 50 steps) and the oracle vs "
+                        "central differences: tests"}
+
+
 def run_reference(a):
     rank, world, _ = _dist()
     if rank != 0:
@@ -394,6 +470,7 @@ def main():
             "error": "relative L2 vs the fp64 oracle: see the 256^3 x 1000-step precision test"}
 
     serving = _serving(a, seisgb, synth, value) if a.serve_requests > 0 else None
+    gradient = _gradient(a, seisgb, synth, peak) if a.grad_shots > 0 else None
 
     # end to end through the C ABI with pinned host buffers: velocity and wavelet
     # copied in, traces copied out, every step
@@ -435,6 +512,7 @@ def main():
         "clocks": clk,
         "precision": precision,
         "serving": serving,
+        "gradient": gradient,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle

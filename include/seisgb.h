@@ -130,14 +130,17 @@ int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int
  * (the paper has no adjoint; the derivation is in the oracle and the design
  * notes).  The forward run keeps (u^n, u^{n-1}, phi^n) every ckpt_every steps
  * (0: 100); the backward sweep recomputes each segment's forward steps and
- * runs the adjoint steps over it.  The misfit sum and the time accumulation of
- * the gradient are fp64; everything else fp32 (SGB_FP32 storage only).
+ * runs the adjoint steps over it.  The misfit sum is fp64; the time sum of the
+ * gradient is fp32 per point over blocks of 32 steps (counted from step 0, so
+ * the result does not depend on ckpt_every) and fp64 across blocks;
+ * everything else fp32 (SGB_FP32 storage only).
  *   velocity  Nz*Ny*Nx fp32 compact, host or device
  *   wavelet   nt fp32, host or device;  src_ijk, rec_ijk: host
  *   observed  nt*nrec fp32 (same layout as run_shot's traces), host or device
  *   misfit_out     host double
  *   grad_velocity  Nz*Ny*Nx fp64 compact, host or device
- * Scratch: 9 padded fields, ceil(nt / ckpt_every) x 3 checkpoint fields and
+ * Scratch: 9 padded fp32 fields and one fp64 field, ceil(nt / ckpt_every) x 3
+ * checkpoint fields and
  * ckpt_every recomputation fields, from the library pool.  Synchronous. */
 int adjoint_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
                  const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec,

@@ -13,72 +13,37 @@
 //           neighbours, c_a / (2 h_a) = k_a (d(+1)^2 - d(-1)^2) / (1 + e)
 //   dJ/dm += w^k g^{k-1} / m,   g^n = L u^n + phi^n + f^n
 // i.e. the forward step run backward in time with the trace residual r
-// injected at the receivers.  dJ/dv = dJ/dm * 2 v dt^2 (dt held fixed).
+// injected at the receivers.  dJ/dv = dJ/dm * 2 v dt^2 = 2 (sum_k w^k g^{k-1}) / v
+// (dt held fixed, m = (v dt)^2).
+//
+// The GPU keeps mu = nu / (1 + e) instead of nu: then mu^k = (mu^{k+1} +
+// w^{k+1}) / (1 + e) and psi = sum_a k_a [G_a mu^{k+1}](x + e_a) - [G_a
+// mu^{k+1}](x - e_a) with G_a(y) = d_a(y+1)^2 - d_a(y-1)^2, both computed by the
+// adjoint step kernel at its PML tiles (mu is zero off the PML).  The time sum
+// sum_k w^k g^{k-1} runs in fp32 per point over blocks of FOLD_EVERY steps
+// (counted from step 0, so the grouping does not depend on the checkpoint
+// interval) and is folded into an fp64 sum after each block.
 #pragma once
 
 namespace {
 
-using CfgAdj = TileCfg<SGB_TXT, SGB_TYT, SGB_TY, SGB_NU, 3, SGB_MINB, SGB_UNROLL>;
+using CfgAdj = TileCfg<SGB_TXT, SGB_TYT, SGB_TY, SGB_NU, 2, SGB_MINB, SGB_UNROLL>;
+constexpr int FOLD_EVERY = 32;
 
-// psi from nu^{k+1} on the PML and the inner points next to it; nu^k on the
-// PML.  One thread per computed point (points far from the PML return).
-__global__ void psi_nu_kernel(StepArgs a, const float *__restrict__ w1,
-                              const float *__restrict__ nu_in, float *__restrict__ nu_out,
-                              float *__restrict__ psi)
+// G += S, S = 0 over the padded arrays (the fp64 time sum of the gradient).
+__global__ void fold_kernel(float *__restrict__ S, double *__restrict__ G, long long n)
 {
-    const long long npts = (long long)a.Nx * a.Ny * a.Nz;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const int nin[3] = {a.nx, a.ny, a.nz};
-    const float ka[3] = {a.kx, a.ky, a.kz};
-    const float ea[3] = {a.ax, a.ay, a.az};
-    const long long st3[3] = {1, a.sx, a.sxy};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < npts; c += stride) {
-        const int i = (int)(c % a.Nx);
-        const long long t = c / a.Nx;
-        const int j = (int)(t % a.Ny), k = (int)(t / a.Ny);
-        const int x[3] = {i, j, k};
-        int d[3];
-        bool pml = false, band = false;
-        for (int q = 0; q < 3; ++q) {
-            d[q] = pml_depth(nin[q], a.nb, x[q]);
-            pml |= d[q] > 0;
-            band |= x[q] == a.nb || x[q] == a.nb + nin[q] - 1;
-        }
-        if (!pml && !band) continue;
-        const long long p = a.origin + (long long)k * a.sxy + (long long)j * a.sx + i;
-        float s = 0.0f;
-        for (int ax = 0; ax < 3; ++ax)
-            for (int sg = -1; sg <= 1; sg += 2) {
-                int y[3] = {x[0], x[1], x[2]};
-                y[ax] += sg;
-                if (y[ax] < 0 || y[ax] >= (ax == 0 ? a.Nx : ax == 1 ? a.Ny : a.Nz)) continue;
-                int dy[3];
-                float e = 0.0f;
-                bool ypml = false;
-                for (int q = 0; q < 3; ++q) {
-                    dy[q] = pml_depth(nin[q], a.nb, y[q]);
-                    ypml |= dy[q] > 0;
-                    e += ea[q] * float(dy[q] * dy[q]);
-                }
-                if (!ypml) continue;
-                const int dp = pml_depth(nin[ax], a.nb, y[ax] + 1);
-                const int dm = pml_depth(nin[ax], a.nb, y[ax] - 1);
-                const float cy = ka[ax] * float(dp * dp - dm * dm) / (1.0f + e);
-                s += float(sg) * cy * nu_in[p + sg * st3[ax]];
-            }
-        psi[p] = s;
-        if (pml) {
-            float e = 0.0f;
-            for (int q = 0; q < 3; ++q) e += ea[q] * float(d[q] * d[q]);
-            nu_out[p] = nu_in[p] / (1.0f + e) + w1[p];
-        }
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        G[q] += (double)S[q];
+        S[q] = 0.0f;
     }
 }
 
-// Residual of step k-1 enters at the receivers: w^k += m r, and the gradient
-// term of that part (m r g / m = r g).
+// Residual of step k-1 enters at the receivers: w^k += m r, and its term of
+// the gradient sum, S += (m r) g^{k-1}.
 __global__ void inject_residual_kernel(float *__restrict__ w, const float *__restrict__ m,
-                                       const float *__restrict__ acc, double *__restrict__ grad_m,
+                                       const float *__restrict__ acc, float *__restrict__ S,
                                        const long long *__restrict__ rec_off, int nrec,
                                        const float *__restrict__ traces_row,
                                        const float *__restrict__ obs_row)
@@ -86,9 +51,9 @@ __global__ void inject_residual_kernel(float *__restrict__ w, const float *__res
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < nrec) {
         const long long p = rec_off[r];
-        const float res = traces_row[r] - obs_row[r];
-        w[p] += m[p] * res;
-        grad_m[p] += (double)res * (double)acc[p];
+        const float add = m[p] * (traces_row[r] - obs_row[r]);
+        w[p] += add;
+        S[p] = fmaf(add, acc[p], S[p]);
     }
 }
 
@@ -125,21 +90,21 @@ __global__ void misfit_final_kernel(const double *partial, int n, double *J)
     }
 }
 
-// dJ/dv = dJ/dm * 2 v dt^2 on the compact grid.
-__global__ void chain_kernel(PadGeom g, const double *__restrict__ grad_m,
-                             const float *__restrict__ vel, float dt, double *__restrict__ grad_v)
+// dJ/dv = 2 (sum_k w^k g^{k-1}) / v on the compact grid.
+__global__ void chain_kernel(PadGeom g, const double *__restrict__ G,
+                             const float *__restrict__ vel, double *__restrict__ grad_v)
 {
     const long long n = (long long)g.Nx * g.Ny * g.Nz;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
         const long long i = c % g.Nx, t = c / g.Nx;
         const long long j = t % g.Ny, k = t / g.Ny;
-        const double v = vel[c];
-        grad_v[c] = grad_m[g.origin + k * g.sxy + j * g.sx + i] * 2.0 * v * (double)dt * (double)dt;
+        grad_v[c] = 2.0 * G[g.origin + k * g.sxy + j * g.sx + i] / (double)vel[c];
     }
 }
 
 int adjoint_prepared = 0;
+int adjoint_occ = 0;  // resident adjoint-step CTAs per SM
 
 }  // namespace
 
@@ -175,6 +140,10 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
         CUDA_TRY(cudaFuncSetAttribute(adjoint_step_kernel<CfgAdj>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)Stage<CfgAdj, float, MODE_ADJ>::SMEM_BYTES));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &adjoint_occ, adjoint_step_kernel<CfgAdj>, CfgAdj::BLOCK,
+            Stage<CfgAdj, float, MODE_ADJ>::SMEM_BYTES));
+        if (adjoint_occ < 1) return fail(SGB_ERR_CUDA, "adjoint step kernel does not fit on an SM");
         adjoint_prepared = 1;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -219,23 +188,24 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
         return fail(SGB_ERR_UNSTABLE_DT, "dt %g above the CFL limit %g of the model", (double)g->dt,
                     cfl_limit(g, vmax_model));
     // fields
-    float *u0, *u1, *phi, *m, *w0, *w1, *nu0, *nu1, *psi, *ck, *seg, *d_tr;
-    double *grad_m, *d_J;
+    float *u0, *u1, *phi, *m, *w0, *w1, *mu0, *mu1, *gsum, *ck, *seg, *d_tr;
+    double *gsum64, *d_J;
     long long *d_off;
     if ((rc = sc.get((void **)&u0, fbytes)) || (rc = sc.get((void **)&u1, fbytes)) ||
         (rc = sc.get((void **)&phi, fbytes)) || (rc = sc.get((void **)&m, fbytes)) ||
         (rc = sc.get((void **)&w0, fbytes)) || (rc = sc.get((void **)&w1, fbytes)) ||
-        (rc = sc.get((void **)&nu0, fbytes)) || (rc = sc.get((void **)&nu1, fbytes)) ||
-        (rc = sc.get((void **)&psi, fbytes)) ||
+        (rc = sc.get((void **)&mu0, fbytes)) || (rc = sc.get((void **)&mu1, fbytes)) ||
+        (rc = sc.get((void **)&gsum, fbytes)) ||
         (rc = sc.get((void **)&ck, fbytes * 3 * (size_t)nseg)) ||
         (rc = sc.get((void **)&seg, fbytes * (size_t)C)) ||
         (rc = sc.get((void **)&d_tr, (size_t)nt * nrec * 4)) ||
-        (rc = sc.get((void **)&grad_m, (size_t)L.elems * 8)) || (rc = sc.get((void **)&d_J, 8)) ||
+        (rc = sc.get((void **)&gsum64, (size_t)L.elems * 8)) || (rc = sc.get((void **)&d_J, 8)) ||
         (rc = sc.get((void **)&d_off, (size_t)nrec * 8)))
         return rc;
     CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), (size_t)nrec * 8, cudaMemcpyHostToDevice, st));
-    for (float *f : {u0, u1, phi, m, w0, w1, nu0, nu1, psi}) CUDA_TRY(cudaMemsetAsync(f, 0, fbytes, st));
-    CUDA_TRY(cudaMemsetAsync(grad_m, 0, (size_t)L.elems * 8, st));
+    for (float *f : {u0, u1, phi, m, w0, w1, mu0, mu1, gsum})
+        CUDA_TRY(cudaMemsetAsync(f, 0, fbytes, st));
+    CUDA_TRY(cudaMemsetAsync(gsum64, 0, (size_t)L.elems * 8, st));
     CUDA_TRY(cudaMemsetAsync(d_J, 0, 8, st));
     make_m_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), d_vel, g->dt, m);
     CUDA_TRY(cudaGetLastError());
@@ -284,21 +254,25 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
 
     // 2. backward sweep, segment by segment from the last
     float *wbuf[2] = {w0, w1};  // w^k lives in wbuf[k & 1]
-    float *nbuf[2] = {nu0, nu1};
+    float *mbuf[2] = {mu0, mu1};  // mu^k lives in mbuf[k & 1]
     std::vector<CUtensorMap> acc_maps(C);
     for (int q = 0; q < C; ++q)
         if ((rc = encode_map<float>(&acc_maps[q], seg + (size_t)q * L.elems, L, CfgAdj::BX, CfgAdj::BY)))
             return rc;
-    StepMaps amaps[2];  // [k & 1]: reads w^{k+1} = wbuf[(k+1)&1], writes wbuf[k&1]
+    // [k & 1]: reads w^{k+1} = wbuf[(k+1)&1] and mu^{k+1}, writes wbuf[k&1]
+    StepMaps amaps[2];
     for (int p = 0; p < 2; ++p)
-        if ((rc = encode_step_maps<float>(amaps[p], wbuf[(p + 1) & 1], wbuf[p & 1], m, psi, L))) return rc;
+        if ((rc = encode_step_maps<float>(amaps[p], wbuf[(p + 1) & 1], wbuf[p & 1], m,
+                                          mbuf[(p + 1) & 1], L)))
+            return rc;
+    CUtensorMap gs_map;
+    if ((rc = encode_map<float>(&gs_map, gsum, L, CfgAdj::BX, CfgAdj::BY))) return rc;
     StepArgs abase = base;
-    abase.phi = nullptr;
     abase.sk = -1;  // the adjoint's sources are the receivers (injected separately)
-    abase.grad_m = grad_m;
+    abase.gsum = gsum;
     int agrid = 0;
-    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, ds->occ, abase, &agrid);
-    const int pgrid = ew_grid(ncomp, *ds);
+    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, adjoint_occ, abase, &agrid);
+    const int fgrid = ew_grid(L.elems, *ds);
     for (int s = nseg - 1; s >= 0; --s) {
         const int na = s * C, nbnd = std::min(na + C, nt);
         const float *src_ck = ck + (size_t)s * 3 * L.elems;
@@ -321,27 +295,31 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
             StepArgs a = abase;
             a.u_out = wbuf[k & 1];
             a.u_cur = wbuf[(k + 1) & 1];
+            a.phi = mbuf[k & 1];
+            a.mu_in = mbuf[(k + 1) & 1];
             a.step_add = k;
-            psi_nu_kernel<<<pgrid, 256, 0, st>>>(a, wbuf[(k + 1) & 1], nbuf[(k + 1) & 1],
-                                                  nbuf[k & 1], psi);
-            CUDA_TRY(cudaGetLastError());
             const StepMaps &mp = amaps[k & 1];
             adjoint_step_kernel<CfgAdj><<<agrid, CfgAdj::BLOCK,
                                           Stage<CfgAdj, float, MODE_ADJ>::SMEM_BYTES, st>>>(
-                a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi, acc_maps[k - 1 - na]);
+                a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi, acc_maps[k - 1 - na], gs_map);
             CUDA_TRY(cudaGetLastError());
             inject_residual_kernel<<<(nrec + 255) / 256, 256, 0, st>>>(
-                wbuf[k & 1], m, seg + (size_t)(k - 1 - na) * L.elems, grad_m, d_off, nrec,
+                wbuf[k & 1], m, seg + (size_t)(k - 1 - na) * L.elems, gsum, d_off, nrec,
                 d_tr + (size_t)(k - 1) * nrec, d_obs + (size_t)(k - 1) * nrec);
             CUDA_TRY(cudaGetLastError());
-            t_launches += 3;
+            t_launches += 2;
+            if ((k - 1) % FOLD_EVERY == 0) {  // blocks of steps counted from step 0
+                fold_kernel<<<fgrid, 256, 0, st>>>(gsum, gsum64, (long long)L.elems);
+                CUDA_TRY(cudaGetLastError());
+                ++t_launches;
+            }
         }
     }
     // 3. chain rule to velocity, outputs
     double *d_gv = grad_velocity;
     const bool host_gv = !is_device_ptr(grad_velocity);
     if (host_gv && (rc = sc.get((void **)&d_gv, (size_t)ncomp * 8))) return rc;
-    chain_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), grad_m, d_vel, g->dt, d_gv);
+    chain_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), gsum64, d_vel, d_gv);
     CUDA_TRY(cudaGetLastError());
     if (host_gv)
         CUDA_TRY(cudaMemcpyAsync(grad_velocity, d_gv, (size_t)ncomp * 8, cudaMemcpyDeviceToHost, st));

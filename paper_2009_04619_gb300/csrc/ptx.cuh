@@ -106,6 +106,21 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Approximate reciprocal (the PTX rcp.approx instruction, about 1 ulp); used
+// for 1 / (1 + eta dt), whose argument lies in [1, 2].
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 16-byte read-only global load (the address must be 16-byte aligned).
+__device__ __forceinline__ float4 ldg128(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+
 __device__ __forceinline__ float4 lds128(const float *p)
 {
     return *reinterpret_cast<const float4 *>(p);

@@ -258,7 +258,8 @@ struct TmaType<__nv_bfloat16> {
 
 // 3D tiled map over the computed region of a padded field of element type T.
 template <class T>
-int encode_map(CUtensorMap *map, const void *padded, const sgb_layout_info &L, int box_x, int box_y)
+int encode_map(CUtensorMap *map, const void *padded, const sgb_layout_info &L, int box_x, int box_y,
+               CUtensorMapL2promotion promo = SGB_L2PROMO_P)
 {
     const size_t es = sizeof(T);
     void *base = const_cast<char *>(static_cast<const char *>(padded)) + L.origin * es;
@@ -268,7 +269,7 @@ int encode_map(CUtensorMap *map, const void *padded, const sgb_layout_info &L, i
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(map, TmaType<T>::v, 3, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          SGB_L2PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SGB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return SGB_OK;
 }
@@ -283,7 +284,7 @@ int encode_step_maps(StepMaps &mp, const void *u_cur, const void *u_prev, const 
 {
     using G = Stage<Cfg, T>;
     int rc;
-    if ((rc = encode_map<T>(&mp.ucur, u_cur, L, G::SW, Cfg::SH))) return rc;
+    if ((rc = encode_map<T>(&mp.ucur, u_cur, L, G::SW, Cfg::SH, SGB_L2PROMO))) return rc;
     if ((rc = encode_map<T>(&mp.ucur_in, u_cur, L, Cfg::BX, Cfg::BY))) return rc;
     if ((rc = encode_map<T>(&mp.uprev, u_prev, L, Cfg::BX, Cfg::BY))) return rc;
     if ((rc = encode_map<float>(&mp.m, m, L, Cfg::BX, Cfg::BY))) return rc;

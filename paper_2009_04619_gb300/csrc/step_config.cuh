@@ -31,8 +31,17 @@ namespace sgb {
 #ifndef SGB_MINB
 #define SGB_MINB 2
 #endif
+// L2 promotion of the tensor maps: the u^n box with its x-y halo (the
+// halos are shared with neighbouring tiles, so wider L2 fills are reused),
+// and the halo-free tiles (u^{n-1}, m, phi, ...), whose rows are whole 32-byte
+// sectors that no other tile reads: promoting those fetched sectors nobody
+// used (measured on 256^3 + 16-point PML: 14 MB less DRAM read per step
+// without promotion, 2% faster on 512^3).
 #ifndef SGB_L2PROMO
 #define SGB_L2PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+#endif
+#ifndef SGB_L2PROMO_P
+#define SGB_L2PROMO_P CU_TENSOR_MAP_L2_PROMOTION_NONE
 #endif
 using Cfg = TileCfg<SGB_TXT, SGB_TYT, SGB_TY, SGB_NU, SGB_NP, SGB_MINB, SGB_UNROLL>;
 

@@ -69,6 +69,9 @@ enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_RANGE = 4 };
 // the adjoint step (see adjoint notes below).
 enum : int { MODE_FWD = 0, MODE_FWD_ACC = 1, MODE_ADJ = 2 };
 
+// Plane kinds of a work unit (compile-time paths of the plane body).
+enum : int { PLANE_INTERIOR = 0, PLANE_XY = 1, PLANE_Z = 2 };
+
 // Scale state of a 16-bit wavefield pair (device memory): s[k & 3] is the
 // scale of u^k (stored value = u^k / s), mx[k & 3] is max |u^k|.
 struct ScaleState {
@@ -99,7 +102,8 @@ struct StepArgs {
     float *traces;
     ScaleState *scale;     // fp16 storage only
     float *acc_out;        // MODE_FWD_ACC: g = L u^n + phi^n + f^n (padded fp32)
-    double *grad_m;        // MODE_ADJ: dJ/dm accumulated in fp64 (padded)
+    float *gsum;           // MODE_ADJ: fp32 partial sum of w^k g^{k-1} (padded)
+    const float *mu_in;    // MODE_ADJ: mu^{k+1} (padded); phi is mu^k
     int *err;              // device error word
     int tiles_x, tiles_y, zc;
 };
@@ -246,8 +250,8 @@ struct Stage {
     static constexpr int SW = C::BX + 2 * HX;      // u^n box width (elements)
     static constexpr int U_BYTES = align128(SW * C::SH * (int)sizeof(T));
     static constexpr int UP_BYTES = align128(C::P_TILE * (int)sizeof(T));
-    static constexpr int F_BYTES = C::P_TILE * 4;  // one fp32 tile (m, phi / psi, g)
-    static constexpr int P_BYTES = UP_BYTES + (MODE == MODE_ADJ ? 3 : 2) * F_BYTES;
+    static constexpr int F_BYTES = C::P_TILE * 4;  // one fp32 tile (m, phi / mu, g, S)
+    static constexpr int P_BYTES = UP_BYTES + (MODE == MODE_ADJ ? 4 : 2) * F_BYTES;
     static constexpr size_t SMEM_BYTES = size_t(C::NU) * U_BYTES + size_t(C::NP) * P_BYTES +
                                          size_t(C::NU + C::NP) * 16 +
                                          size_t(C::NU + C::NP + 1) * 4;
@@ -314,7 +318,7 @@ struct StepCta {
     using E = Elem<T>;
     using G = Stage<C, T, MODE>;
     // the adjoint's PML-path band is one point wider: inner points next to the
-    // PML receive psi
+    // PML receive psi from their PML neighbours
     static constexpr int BAND = MODE == MODE_ADJ ? 1 : 0;
     static constexpr bool SCALED = E::SCALED;
     static constexpr int TXT = C::TXT, TY = C::TY, NU = C::NU, NP = C::NP;
@@ -324,7 +328,7 @@ struct StepCta {
     static constexpr uint64_t WAIT_NS = 2000000000ull;
 
     const StepArgs *pa;  // the kernel argument, in the constant parameter space
-    const CUtensorMap *tm_ucur, *tm_ucur_in, *tm_uprev, *tm_m, *tm_phi, *tm_acc;
+    const CUtensorMap *tm_ucur, *tm_ucur_in, *tm_uprev, *tm_m, *tm_phi, *tm_acc, *tm_gs;
     unsigned char *su, *sp;  // u ring, (u^{n-1}, m, phi) ring
     uint64_t *full_u, *empty_u, *full_p, *empty_p;
     int *lastf_u, *lastf_p, *s_abort;
@@ -333,6 +337,56 @@ struct StepCta {
     bool xy_inner, aborted, store_ok;
     float s_cur, s_prev, inv_s_next;  // fp16 scales (1 otherwise)
     float vmax;                       // running max |u^{n+1}| of this thread
+    // PML terms of the thread's fixed columns i = gi + e and rows j = gj0 + r:
+    // eta dt = a d(i)^2, the gradient factor k (d(i+1)^2 - d(i-1)^2), the
+    // adjoint's k G(i +- 1) with G(y) = d(y+1)^2 - d(y-1)^2, and PML masks
+    float pex[4], pgx[4], phxp[4], phxm[4];
+    float pey[TY], pgy[TY], phyp[TY], phym[TY];
+    int pmx, pmy;
+    // 1 / (1 + e) and 1 - e of the thread's points in planes outside the z-PML
+    // (e = eta dt depends on x and y only there)
+    float pinv[TY][4], pome[TY][4];
+
+    __device__ __forceinline__ void pml_axis(int n_in, int i, float ca, float ck, float &e, float &gk,
+                                             float &hp, float &hm, bool &in_pml) const
+    {
+        const int nb = pa->nb;
+        const int d = pml_depth(n_in, nb, i), dp = pml_depth(n_in, nb, i + 1);
+        const int dm = pml_depth(n_in, nb, i - 1);
+        const int d2p = pml_depth(n_in, nb, i + 2), d2m = pml_depth(n_in, nb, i - 2);
+        e = __fmul_rn(ca, float(d * d));
+        gk = __fmul_rn(ck, float(dp * dp - dm * dm));
+        hp = __fmul_rn(ck, float(d2p * d2p - d * d));
+        hm = __fmul_rn(ck, float(d * d - d2m * d2m));
+        in_pml = d > 0;
+    }
+
+    // Every PML-path operation below has an explicit rounding (fmaf, __fmul_rn,
+    // __fadd_rn): implicit contraction may differ between the kernels that
+    // inline this code, and the serving kernel must reproduce run_shot to the bit.
+    __device__ __forceinline__ void pml_tables()
+    {
+        const StepArgs &a = *pa;
+        pmx = pmy = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            bool in;
+            pml_axis(a.nx, gi + e, a.ax, a.kx, pex[e], pgx[e], phxp[e], phxm[e], in);
+            pmx |= int(in) << e;
+        }
+#pragma unroll
+        for (int r = 0; r < TY; ++r) {
+            bool in;
+            pml_axis(a.ny, gj0 + r, a.ay, a.ky, pey[r], pgy[r], phyp[r], phym[r], in);
+            pmy |= int(in) << r;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float exy = __fadd_rn(pex[e], pey[r]);
+                pinv[r][e] = rcp_approx(__fadd_rn(1.0f, exy));
+                pome[r][e] = __fsub_rn(1.0f, exy);
+            }
+        }
+    }
 
     __device__ __forceinline__ bool plane_pml(int k) const
     {
@@ -383,15 +437,17 @@ struct StepCta {
         if (f > 0) wait(empty_p + s, (f - 1) & 1);
         lastf_p[s] = f;
         const bool pml = plane_pml(k);
-        const int ntiles = (pml ? 2 : 1) + (MODE == MODE_ADJ ? 1 : 0);
+        const int ntiles = (pml ? 2 : 1) + (MODE == MODE_ADJ ? 2 : 0);
         mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + ntiles * G::F_BYTES);
         unsigned char *d = sp + s * G::P_BYTES;
         const uint64_t pol = policy_evict_first();
         tma_load_3d_hint(d, tm_uprev, full_p + s, x0, y0, k, pol);
         tma_load_3d_hint(d + G::UP_BYTES, tm_m, full_p + s, x0, y0, k, pol);
         if (pml) tma_load_3d_hint(d + G::UP_BYTES + G::F_BYTES, tm_phi, full_p + s, x0, y0, k, pol);
-        if constexpr (MODE == MODE_ADJ)  // g^{k-1} of the forward recomputation, plane k
+        if constexpr (MODE == MODE_ADJ) {  // g^{k-1} of the recomputation; partial sum S
             tma_load_3d_hint(d + G::UP_BYTES + 2 * G::F_BYTES, tm_acc, full_p + s, x0, y0, k, pol);
+            tma_load_3d_hint(d + G::UP_BYTES + 3 * G::F_BYTES, tm_gs, full_p + s, x0, y0, k, pol);
+        }
     }
 
     // Producer lane: every plane of u^n (z0-4 .. z1+3) and every (u^{n-1}, m,
@@ -418,9 +474,14 @@ struct StepCta {
     // One z-plane: iteration it (plane k = z0 + it).  The queue holds planes
     // k-4 .. k+3 at q[O .. O+7]; the front plane k+4 is loaded into q[O+8].
     // Queue values are the stored (scaled) values; true u = stored * s_cur.
-    template <int O, bool PML>
+    // KIND: PLANE_INTERIOR (no PML point in the tile's plane), PLANE_XY (PML
+    // path, plane outside the z-PML: e from the thread's tables), PLANE_Z (a
+    // z-PML plane).
+    template <int O, int KIND>
     __device__ __forceinline__ void plane(float4 (&q)[TY][QN], int it)
     {
+        constexpr bool PML = KIND != PLANE_INTERIOR;
+        constexpr bool ZP = KIND == PLANE_Z;
         const StepArgs &a = *pa;
         const int k = z0 + it;
         const int relf = it + 8;
@@ -437,6 +498,7 @@ struct StepCta {
         const float *pm = reinterpret_cast<const float *>(pu + G::UP_BYTES);
         const float *pph = reinterpret_cast<const float *>(pu + G::UP_BYTES + G::F_BYTES);
         const float *pg = reinterpret_cast<const float *>(pu + G::UP_BYTES + 2 * G::F_BYTES);
+        const float *pgs = reinterpret_cast<const float *>(pu + G::UP_BYTES + 3 * G::F_BYTES);
 
         // 25-point Laplacian (Eq. 3): centre and z part from the queue
         float4 L[TY], gy[TY];
@@ -464,14 +526,9 @@ struct StepCta {
                 if (PML && d == r + 1) f4fma(gy[r], 1.0f, v);
             }
         }
-        int dzk = 0;
-        float ez = 0.f, gzk = 0.f;
-        if (PML) {
-            dzk = pml_depth(a.nz, a.nb, k);
-            const int dzp = pml_depth(a.nz, a.nb, k + 1), dzm = pml_depth(a.nz, a.nb, k - 1);
-            ez = a.az * float(dzk * dzk);
-            gzk = a.kz * float(dzp * dzp - dzm * dzm);
-        }
+        float ez = 0.f, gzk = 0.f, hzp = 0.f, hzm = 0.f;
+        bool zin = false;
+        if (PML) pml_axis(a.nz, k, a.az, a.kz, ez, gzk, hzp, hzm, zin);
         const long long off0 = base_off + (long long)k * a.sxy;
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
@@ -512,34 +569,66 @@ struct StepCta {
             if (PML) {
                 ph = lds128(pph + pr);
                 phn = ph;
-                const int dyj = pml_depth(a.ny, a.nb, j);
-                const int dyp = pml_depth(a.ny, a.nb, j + 1), dym = pml_depth(a.ny, a.nb, j - 1);
-                const float eyz = fmaf(a.ay, float(dyj * dyj), ez);
-                const float gyk = a.ky * float(dyp * dyp - dym * dym);
+                const float eyz = ZP ? __fadd_rn(pey[r], ez) : 0.0f;
+                const float gyk = pgy[r];
+                // bit e: point e of this row is a PML point
+                const int rowmask = (ZP || zin || ((pmy >> r) & 1)) ? 0xF : pmx;
                 const float4 zp = q[r][O + 5], zm = q[r][O + 3];
+                // adjoint: psi = sum_a k_a [G_a mu](x + e_a) - [G_a mu](x - e_a) from the six
+                // neighbours of mu^{k+1} (zero outside the PML and in the halo)
+                float4 myp = make_float4(0.f, 0.f, 0.f, 0.f), mym = myp, mzp = myp, mzm = myp;
+                float mxl = 0.f, mxr = 0.f;
+                if constexpr (MODE == MODE_ADJ) {
+                    if (store_ok && j < a.Ny) {
+                        const float *mc = a.mu_in + off0 + (long long)r * a.sx;
+                        myp = ldg128(mc + a.sx);
+                        mym = ldg128(mc - a.sx);
+                        mzp = ldg128(mc + a.sxy);
+                        mzm = ldg128(mc - a.sxy);
+                        mxl = __ldg(mc - 1);
+                        mxr = __ldg(mc + 4);
+                    }
+                }
+                const float mux[6] = {mxl, ph.x, ph.y, ph.z, ph.w, mxr};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int i = gi + e;
-                    const int dxi = pml_depth(a.nx, a.nb, i);
-                    const int dxp = pml_depth(a.nx, a.nb, i + 1), dxm = pml_depth(a.nx, a.nb, i - 1);
-                    const bool pt = (dxi | dyj | dzk) != 0;
+                    const bool pt = (rowmask >> e) & 1;
                     any_pml |= pt;
-                    const float edt = fmaf(a.ax, float(dxi * dxi), eyz);
-                    float Gd = a.kx * float(dxp * dxp - dxm * dxm) * (w[5 + e] - w[3 + e]) +
-                               gyk * f4get(gy[r], e) + gzk * (f4get(zp, e) - f4get(zm, e));
-                    if constexpr (SCALED) Gd *= s_cur;
-                    const float inv = __frcp_rn(1.0f + edt);
+                    float Gd = fmaf(pgx[e], __fsub_rn(w[5 + e], w[3 + e]),
+                                    fmaf(gyk, f4get(gy[r], e),
+                                         __fmul_rn(gzk, __fsub_rn(f4get(zp, e), f4get(zm, e)))));
+                    if constexpr (SCALED) Gd = __fmul_rn(Gd, s_cur);
+                    float inv, ome;  // 1 / (1 + e), 1 - e
+                    if constexpr (ZP) {
+                        const float edt = __fadd_rn(pex[e], eyz);
+                        inv = rcp_approx(__fadd_rn(1.0f, edt));
+                        ome = __fsub_rn(1.0f, edt);
+                    } else {
+                        inv = pinv[r][e];
+                        ome = pome[r][e];
+                    }
                     const float cc = f4get(c, e), pe = f4get(ph, e);
-                    const float upml = ((2.0f - edt * edt) * cc - (1.0f - edt) * f4get(up, e) +
-                                        f4get(mm, e) * (f4get(Lr, e) + pe)) * inv;
-                    const float ppml = (pe - Gd) * inv;
+                    float rhs = pe;  // phi^n (forward) or psi (adjoint)
+                    if constexpr (MODE == MODE_ADJ) {
+                        rhs = fmaf(phxp[e], mux[e + 2], __fmul_rn(-phxm[e], mux[e]));
+                        rhs = fmaf(phyp[r], f4get(myp, e), rhs);
+                        rhs = fmaf(-phym[r], f4get(mym, e), rhs);
+                        rhs = fmaf(hzp, f4get(mzp, e), rhs);
+                        rhs = fmaf(-hzm, f4get(mzm, e), rhs);
+                    }
+                    const float lr = __fadd_rn(f4get(Lr, e), rhs);
+                    // [(2 - e^2) c - (1 - e) u^{n-1} + m lr] / (1 + e)
+                    //   = (1 - e) c + [c - (1 - e) u^{n-1} + m lr] / (1 + e)
+                    const float upml =
+                        fmaf(inv, fmaf(f4get(mm, e), lr, fmaf(-ome, f4get(up, e), cc)),
+                             __fmul_rn(ome, cc));
+                    const float ppml = __fmul_rn(__fsub_rn(pe, Gd), inv);
                     ptmask |= int(pt) << e;
                     if constexpr (MODE == MODE_ADJ) {
-                        // adjoint: the phi slot holds psi, which also reaches the
-                        // inner points next to the PML; no phi update here
-                        f4set(un, e, pt ? upml
-                                        : fmaf(f4get(mm, e), f4get(Lr, e) + pe,
-                                               fmaf(2.0f, cc, -f4get(up, e))));
+                        // psi also reaches the inner points next to the PML;
+                        // mu^k = (mu^{k+1} + w^{k+1}) / (1 + e) on the PML
+                        f4set(un, e, pt ? upml : fmaf(f4get(mm, e), lr, fmaf(2.0f, cc, -f4get(up, e))));
+                        if (pt) f4set(phn, e, __fmul_rn(__fadd_rn(pe, cc), inv));
                     } else if (pt) {
                         f4set(un, e, upml);
                         f4set(phn, e, ppml);
@@ -556,7 +645,7 @@ struct StepCta {
             if (MODE != MODE_ADJ && k == a.sk && j == a.sj && a.si >= gi && a.si < gi + 4) {
                 const int e = a.si - gi;
                 const float f = a.wavelet[n] * a.inv_vol;
-                f4set(un, e, f4get(un, e) + f4get(mm, e) * f);
+                f4set(un, e, fmaf(f4get(mm, e), f, f4get(un, e)));
                 if constexpr (MODE == MODE_FWD_ACC) f4set(acc4, e, f4get(acc4, e) + f);
             }
             if (store_ok && j < a.Ny) {
@@ -569,7 +658,7 @@ struct StepCta {
                 T *uo = static_cast<T *>(a.u_out) + off;
                 uint32_t rnd = 0;
                 if constexpr (sizeof(T) == 2) rnd = hash_bits((uint32_t)off, (uint32_t)n);
-                const bool wphi = MODE != MODE_ADJ && PML && any_pml;
+                const bool wphi = PML && any_pml;  // phi^{n+1}, or mu^k in the adjoint
                 if (gi + 3 < a.Nx) {
                     E::st(uo, un, rnd);
                     if (wphi) stg128(a.phi + off, phn);
@@ -582,11 +671,17 @@ struct StepCta {
                     }
                 }
                 if constexpr (MODE == MODE_ADJ) {
-                    // dJ/dm += w^k g^{k-1} / m, accumulated in fp64
+                    // S += w^k g^{k-1} (dJ/dm = sum_k w^k g^{k-1} / m; S is folded
+                    // into the fp64 sum every few steps)
                     const float4 gk = lds128(pg + pr);
-                    for (int e = 0; e < 4 && gi + e < a.Nx; ++e)
-                        a.grad_m[off + e] +=
-                            (double)f4get(un, e) * (double)f4get(gk, e) / (double)f4get(mm, e);
+                    float4 s4 = lds128(pgs + pr);
+                    s4.x = fmaf(un.x, gk.x, s4.x);
+                    s4.y = fmaf(un.y, gk.y, s4.y);
+                    s4.z = fmaf(un.z, gk.z, s4.z);
+                    s4.w = fmaf(un.w, gk.w, s4.w);
+                    if (gi + 3 < a.Nx) stg128(a.gsum + off, s4);
+                    else
+                        for (int e = 0; e < 4 && gi + e < a.Nx; ++e) a.gsum[off + e] = f4get(s4, e);
                 }
             }
         }
@@ -608,28 +703,28 @@ struct StepCta {
             for (int jq = 0; jq < 8; ++jq) q[r][jq] = q[r][jq + O];
     }
 
-    template <int O, bool PML>
+    template <int O, int KIND>
     __device__ __forceinline__ void group(float4 (&q)[TY][QN], int it)
     {
         if constexpr (O < U) {
-            plane<O, PML>(q, it + O);
-            group<O + 1, PML>(q, it);
+            plane<O, KIND>(q, it + O);
+            group<O + 1, KIND>(q, it);
         }
     }
 
     // Iterations [it, it_end) of one kind (PML or interior): groups of U
     // planes with compile-time queue offsets, then single planes.
-    template <bool PML>
+    template <int KIND>
     __device__ __forceinline__ void segment(float4 (&q)[TY][QN], int it, int it_end)
     {
         if (U > 1) {
             for (; it + U <= it_end && !aborted; it += U) {
-                group<0, PML>(q, it);
+                group<0, KIND>(q, it);
                 shift<U>(q);
             }
         }
         for (; it < it_end && !aborted; ++it) {
-            plane<0, PML>(q, it);
+            plane<0, KIND>(q, it);
             shift<1>(q);
         }
     }
@@ -658,6 +753,7 @@ constexpr int min_blocks()
 struct StepMapPtrs {
     const CUtensorMap *ucur, *ucur_in, *uprev, *m, *phi;
     const CUtensorMap *acc;  // MODE_ADJ: g^{k-1}
+    const CUtensorMap *gs;   // MODE_ADJ: partial sum S
 };
 
 // One work unit (tile x z-chunk, index `unit` of `units`) of step n.  With
@@ -682,6 +778,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     st.tm_m = tm.m;
     st.tm_phi = tm.phi;
     st.tm_acc = tm.acc;
+    st.tm_gs = tm.gs;
     st.su = smem_raw;
     st.sp = smem_raw + NU * G::U_BYTES;
     st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES);
@@ -773,6 +870,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     st.prow = (TY * tyi) * BX + 4 * txi;
     st.store_ok = st.gi < a.Nx;
     st.base_off = a.origin + (long long)st.gj0 * a.sx + st.gi;
+    st.pml_tables();
 
     // Prime the register queue with planes z0-4 .. z0+3 (first fill of slots 0..7).
     float4 q[TY][C::QN];
@@ -788,16 +886,24 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
         for (int s = 0; s < 4; ++s) mbar_arrive(st.empty_u + s);
     st.aborted = *reinterpret_cast<volatile int *>(st.s_abort) != 0;
 
-    // z segments: PML planes below the inner region, interior planes, PML
-    // planes above it (all PML for tiles touching the x-y PML band).
-    if (!st.xy_inner) {
-        st.template segment<true>(q, 0, nit);
-    } else {
-        const int a0 = min(max(a.nb + S::BAND - st.z0, 0), nit);
-        const int a1 = min(max(a.nb + a.nz - S::BAND - st.z0, a0), nit);
-        st.template segment<true>(q, 0, a0);
-        st.template segment<false>(q, a0, a1);
-        st.template segment<true>(q, a1, nit);
+    // z segments: z-PML planes below the inner region, then the planes
+    // outside the z-PML (interior path, or the PML path for tiles touching the
+    // x-y PML band and for the adjoint's band planes next to the z-PML), then
+    // the z-PML planes above it.
+    {
+        const int zlo = min(max(a.nb - st.z0, 0), nit);
+        const int zhi = min(max(a.nb + a.nz - st.z0, zlo), nit);
+        st.template segment<PLANE_Z>(q, 0, zlo);
+        if (!st.xy_inner) {
+            st.template segment<PLANE_XY>(q, zlo, zhi);
+        } else {
+            const int b0 = min(max(a.nb + S::BAND - st.z0, zlo), zhi);
+            const int b1 = min(max(a.nb + a.nz - S::BAND - st.z0, b0), zhi);
+            st.template segment<PLANE_XY>(q, zlo, b0);
+            st.template segment<PLANE_INTERIOR>(q, b0, b1);
+            st.template segment<PLANE_XY>(q, b1, zhi);
+        }
+        st.template segment<PLANE_Z>(q, zhi, nit);
     }
 
     if constexpr (S::SCALED) {  // max |u^{n+1}| for the next step's scale
@@ -818,7 +924,7 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
                       const __grid_constant__ CUtensorMap tm_m,
                       const __grid_constant__ CUtensorMap tm_phi)
 {
-    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr};
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     step_unit<C, T>(a, tm, blockIdx.x, gridDim.x, n, false);
 }
@@ -832,13 +938,14 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
                    const __grid_constant__ CUtensorMap tm_m,
                    const __grid_constant__ CUtensorMap tm_phi)
 {
-    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr};
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     step_unit<C, float, MODE_FWD_ACC>(a, tm, blockIdx.x, gridDim.x, a.step_add, false);
 }
 
 // Adjoint step k (see the adjoint notes in adjoint.cuh): reads w^{k+1} through
-// the u^n maps, w^{k+2} through the u^{n-1} map (overwritten with w^k), psi
-// through the phi map and g^{k-1} through the acc map.
+// the u^n maps, w^{k+2} through the u^{n-1} map (overwritten with w^k),
+// mu^{k+1} through the phi map (mu^k is written to a.phi), g^{k-1} through the
+// acc map and the partial gradient sum S through the gs map (updated in place).
 template <class C>
 __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     adjoint_step_kernel(const __grid_constant__ StepArgs a,
@@ -846,10 +953,11 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
                         const __grid_constant__ CUtensorMap tm_ucur_in,
                         const __grid_constant__ CUtensorMap tm_uprev,
                         const __grid_constant__ CUtensorMap tm_m,
-                        const __grid_constant__ CUtensorMap tm_psi,
-                        const __grid_constant__ CUtensorMap tm_acc)
+                        const __grid_constant__ CUtensorMap tm_mu,
+                        const __grid_constant__ CUtensorMap tm_acc,
+                        const __grid_constant__ CUtensorMap tm_gs)
 {
-    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_psi, &tm_acc};
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_mu, &tm_acc, &tm_gs};
     step_unit<C, float, MODE_ADJ>(a, tm, blockIdx.x, gridDim.x, a.step_add, false);
 }
 

@@ -155,6 +155,45 @@ def scaled(w: Workload, n_inner: int, nb: int, nt: int, name: str | None = None)
                     rec_every=w.rec_every, cfl_fraction=w.cfl_fraction)
 
 
+# Gradient workload: 256^3 computed (224^3 inner + 16-point PML), h = 10 m, the
+# layered model (seed 2009) times a seeded Gaussian anomaly, 10 Hz Ricker,
+# 2000 steps, 16 shots on a 4 x 4 grid of surface positions 20 m deep,
+# receivers on every 4th inner surface point, checkpoints every 100 steps.
+GRADIENT = Workload(name="grad256_pml16_layered_anomaly_ricker10_nt2000_16shots", nx=224, ny=224,
+                    nz=224, nb=16, h=10.0, nt=2000, fp=10.0, model="layered", seed=2009,
+                    rec_every=4, extra={"shots": 16, "ckpt_every": 100, "anomaly_seed": 5})
+
+
+def anomaly_params(w: Workload, seed: int):
+    """Seeded Gaussian anomaly inside the inner region: centre uniform in its
+    middle half, radius U(8, 24) points, amplitude U(5%, 10%) with a random
+    sign.  Returns (centre (i, j, k), radius, amplitude)."""
+    rng = np.random.default_rng(seed)
+    lo = [w.nb + n // 4 for n in (w.nx, w.ny, w.nz)]
+    hi = [w.nb + 3 * n // 4 for n in (w.nx, w.ny, w.nz)]
+    c = tuple(float(rng.uniform(a, b)) for a, b in zip(lo, hi))
+    radius = float(rng.uniform(8.0, 24.0))
+    amp = float(rng.uniform(0.05, 0.10)) * (1.0 if rng.random() < 0.5 else -1.0)
+    return c, radius, amp
+
+
+def gradient_models(w: Workload):
+    """(v, v_obs): the layered model with the anomaly, where the gradient is
+    taken, and the unperturbed layered model that generates the observed data."""
+    v0 = w.velocity()
+    c, radius, amp = anomaly_params(w, w.extra.get("anomaly_seed", 5))
+    v = (v0 * gaussian_anomaly(v0.shape, c, radius, amp)).astype(np.float32)
+    return v, v0
+
+
+def shot_grid(w: Workload, per_side: int = 4, depth: int = 2):
+    """per_side^2 source positions on a regular grid over the inner surface,
+    `depth` points below it."""
+    xs = [w.nb + int((q + 0.5) * w.nx / per_side) for q in range(per_side)]
+    ys = [w.nb + int((q + 0.5) * w.ny / per_side) for q in range(per_side)]
+    return [(x, y, w.nb + depth) for y in ys for x in xs]
+
+
 # Serving workload: shot requests over four grid sizes (computed x, y, z; PML 16).
 SERVE_GRIDS = [(128, 128, 128), (192, 192, 256), (256, 256, 256), (384, 384, 256)]
 
