@@ -2,6 +2,11 @@
 time per launch (CUDA events) -- a small driver for timing and for ncu captures.
 
     python -m paper_2009_04619_gb300.profile_step --n 256 --nb 32 --launches 20
+    python -m paper_2009_04619_gb300.profile_step --adjoint --n 256 --nb 16 --nt 200
+
+With --adjoint it runs one misfit-gradient shot instead (layered model with a
+Gaussian anomaly, observed traces from the model without it) and reports its
+time beside a forward shot of the same length.
 """
 from __future__ import annotations
 
@@ -11,7 +16,40 @@ import json
 import numpy as np
 import torch
 
-from . import build, seisgb
+from . import build, seisgb, synth
+
+
+def _adjoint(a):
+    N, nb = a.n, a.nb
+    n_in = N - 2 * nb
+    shape = (N, N, N)
+    v0 = synth.layered_model(shape, seed=5)
+    v = (v0 * synth.gaussian_anomaly(shape, (N / 2, N / 2, N / 2), N / 12, 0.05)).astype(np.float32)
+    vmax = float(max(v.max(), v0.max()))
+    g0 = seisgb.make_grid(n_in, n_in, n_in, nb, 10.0, 10.0, 10.0, 1.0, vmax)
+    dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, vmax)))
+    g = seisgb.make_grid(n_in, n_in, n_in, nb, 10.0, 10.0, 10.0, dt, vmax)
+    wav = synth.ricker(a.nt, dt, 10.0)
+    src = (N // 2, N // 2, nb + 2)
+    rec = synth.surface_receivers(n_in, n_in, nb, 4)
+    d_v0, d_v = torch.from_numpy(v0).cuda(), torch.from_numpy(v).cuda()
+    d_w = torch.from_numpy(wav).cuda()
+    obs = torch.zeros((a.nt, rec.shape[0]), device="cuda")
+    seisgb.run_shot(g, d_v0, d_w, a.nt, src, rec, obs)
+    grad = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record()
+    J = seisgb.adjoint_shot(g, d_v, d_w, a.nt, src, rec, obs, grad, ckpt_every=a.ckpt)
+    e1.record()
+    seisgb.run_shot(g, d_v, d_w, a.nt, src, rec, obs)
+    e2.record()
+    torch.cuda.synchronize()
+    seisgb.device_status()
+    ta, tf = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    print(json.dumps({"n": N, "nb": nb, "nt": a.nt, "ckpt_every": a.ckpt, "adjoint_ms": ta,
+                      "forward_ms": tf, "ratio": ta / tf, "misfit": J,
+                      "grad_finite": bool(torch.isfinite(grad).all())}))
 
 
 def main(argv=None):
@@ -21,11 +59,17 @@ def main(argv=None):
     p.add_argument("--launches", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--lib", default=None, help="path of an alternative libseisgb.so build")
+    p.add_argument("--adjoint", action="store_true", help="time one misfit-gradient shot")
+    p.add_argument("--nt", type=int, default=200, help="time steps of the gradient shot")
+    p.add_argument("--ckpt", type=int, default=100, help="checkpoint interval of the gradient shot")
     a = p.parse_args(argv)
     if a.lib:
         seisgb.LIB_PATH = a.lib
     else:
         build.build()
+    if a.adjoint:
+        _adjoint(a)
+        return
     n_in = a.n - 2 * a.nb  # nb = 0: no PML, every tile takes the interior path
     h, v = 10.0, 4500.0
     g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, h, h, h, 1.0, v)
