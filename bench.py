@@ -266,8 +266,11 @@ def _gradient(a, seisgb, synth, peak):
     """Adjoint-gradient leg: 16 shots of the 256^3 / 2000-step workload, misfit
     against traces of the unperturbed model, gradients summed over the shots
     (fp64); shots/s, forward-equivalent Gpt/s and the whole computation's
-    algorithmic bytes per second against the HBM peak."""
+    algorithmic bytes per second against the HBM peak.  Under torchrun the shots
+    are split across ranks and one fp64 all-reduce sums the gradients."""
     import torch
+    from paper_2009_04619_gb300 import replicas
+    rank, world, _ = _dist()
     w = synth.GRADIENT
     v, v_obs = synth.gradient_models(w)
     vmax = float(max(v.max(), v_obs.max()))
@@ -278,40 +281,46 @@ def _gradient(a, seisgb, synth, peak):
     wav = synth.ricker(nt, dt, w.fp)
     rec = w.receivers()
     shots = synth.shot_grid(w)[:a.grad_shots]
+    mine = replicas.my_shots(len(shots), rank, world)
     d_v = torch.from_numpy(v).cuda()
     d_vo = torch.from_numpy(v_obs).cuda()
     d_w = torch.from_numpy(wav).cuda()
-    obs = []
-    for src in shots:
+    obs = {}
+    for i in mine:
         o = torch.zeros((nt, rec.shape[0]), dtype=torch.float32, device="cuda")
-        seisgb.run_shot(g, d_vo, d_w, nt, src, rec, o)
-        obs.append(o)
+        seisgb.run_shot(g, d_vo, d_w, nt, shots[i], rec, o)
+        obs[i] = o
     grad = torch.zeros(v.shape, dtype=torch.float64, device="cuda")
-    total = torch.zeros_like(grad)
-    seisgb.adjoint_shot(g, d_v, d_w, nt, shots[0], rec, obs[0], grad, ckpt_every=C)  # warm-up
+
+    def shot_fn(i):
+        return seisgb.adjoint_shot(g, d_v, d_w, nt, shots[i], rec, obs[i], grad, ckpt_every=C), grad
+
+    if mine:
+        shot_fn(mine[0])  # warm-up
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    J = 0.0
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     e0.record(stream)
-    for src, o in zip(shots, obs):
-        J += seisgb.adjoint_shot(g, d_v, d_w, nt, src, rec, o, grad, ckpt_every=C)
-        total += grad
+    J, total = replicas.gradient_sum(shot_fn, len(shots), grad)
     e1.record(stream)
     torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
+    t = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3, device=grad.device)
     tr = torch.zeros((nt, rec.shape[0]), dtype=torch.float32, device="cuda")
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for src in shots[:4]:
+    for src in shots[:2]:
         seisgb.run_shot(g, d_v, d_w, nt, src, rec, tr)
     f1.record(stream)
     torch.cuda.synchronize()
-    t_fwd = f0.elapsed_time(f1) / 1e3 / min(4, len(shots))
+    t_fwd = f0.elapsed_time(f1) / 1e3 / min(2, len(shots))
     ns = len(shots)
     alg = _gradient_alg_bytes(w, nt, C)
     gbs = alg * ns / t / 1e9
     return {"workload": w.name, "grid": list(w.shape), "nb": w.nb, "nt": nt, "shots": ns,
+            "ranks": world, "collective": "one fp64 all-reduce of the gradient" if world > 1 else None,
             "ckpt_every": C, "nrec": int(rec.shape[0]),
             "shots_per_s": ns / t, "ms_per_shot": t / ns * 1e3,
             "gpts_forward_equivalent": w.points * nt * ns / t / 1e9,
@@ -379,7 +388,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    from paper_2009_04619_gb300 import build, seisgb, synth
+    from paper_2009_04619_gb300 import build, replicas, seisgb, synth
     build.build()
     seisgb.lib()
     w = _workload()
@@ -415,14 +424,9 @@ def main():
     barrier()
     launches = seisgb.launch_count(reset=True)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), device=dev)
     ms_per_step = ms / a.steps
-    value = w.points * w.nt * a.steps * world / (ms / 1e3) / 1e9
+    value = replicas.job_rate(w.points * w.nt * a.steps, ms / 1e3, world) / 1e9
 
     # dominant kernel: back-to-back fused steps on the same grid, CUDA events on
     # the launching stream
@@ -460,7 +464,7 @@ def main():
             seisgb.run_shot(gp, d_v, d_w, w.nt, src, rec, d_tr)
         p1.record(stream)
         barrier()
-        pms = p0.elapsed_time(p1) / a.steps
+        pms = replicas.max_over_ranks(p0.elapsed_time(p1), device=dev) / a.steps
         alg16 = _alg_bytes_per_launch(w, wave_bytes=2)
         precision[fname] = {
             "value": w.points * w.nt * world / (pms / 1e3) / 1e9, "unit": UNIT,
@@ -483,13 +487,8 @@ def main():
     for _ in range(a.steps):
         seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
     barrier()
-    e2e_s = time.perf_counter() - t
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_val = w.points * w.nt * a.steps * world / e2e_s / 1e9
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t, device=dev)
+    e2e_val = replicas.job_rate(w.points * w.nt * a.steps, e2e_s, world) / 1e9
     h2d = vel.nbytes + wav.nbytes + rec.nbytes + 12
     d2h = w.nt * nrec * 4
 
