@@ -19,6 +19,11 @@
 // - Composition changes (admission, retirement) happen between replays; the
 //   graph is re-captured only then.  Retired shots' traces are copied to the
 //   host and their device memory returned to the pool.
+// - Each replay ends by bumping a device replay counter, so the host enqueues
+//   several replays back to back and waits only where the composition can
+//   change: up to the next shot completion when no request can be admitted
+//   (slots full), at most MAX_AHEAD_OPEN replays while slots are free (new
+//   arrivals wait at most that long), one replay while an admission is set up.
 #pragma once
 #include <chrono>
 #include <condition_variable>
@@ -29,6 +34,8 @@
 namespace {
 
 constexpr int SERVE_MAX_SLOTS = 64;
+constexpr int MAX_AHEAD_OPEN = 4;     // replays enqueued at once while slots are free
+constexpr int MAX_AHEAD_FULL = 256;   // ... while every slot is taken
 
 // One resident shot as the multi-shot kernel sees it.
 struct alignas(128) ShotEntry {
@@ -44,15 +51,17 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
                  : "memory");
 }
 
-// Launch i of a replay: step n0 + i of every resident shot.
+// Launch i of replay r (r = *replays, counted since the table was uploaded):
+// step n0 + r * steps_per_graph + i of every resident shot.
 __global__ void __launch_bounds__(Cfg::BLOCK, Cfg::MINB)
-    multi_step_kernel(const ShotEntry *__restrict__ table, int nshots, int launch_i)
+    multi_step_kernel(const ShotEntry *__restrict__ table, int nshots, int launch_i,
+                      const int *__restrict__ replays, int steps_per_graph)
 {
     const int b = blockIdx.x;
     int s = 0;
     while (s + 1 < nshots && b >= table[s + 1].unit_begin) ++s;
     const ShotEntry &e = table[s];
-    const int n = e.n0 + launch_i;
+    const int n = e.n0 + *replays * steps_per_graph + launch_i;
     if (n > e.nt) return;  // finished: waits for retirement
     const CUtensorMap *mp = e.maps[n & 1];
     if (threadIdx.x == Cfg::THREADS)  // the producer lane reads the descriptors
@@ -116,6 +125,7 @@ struct sgb_server {
     sgb_serve_stats stats;
     // device table and the graph of the current composition
     ShotEntry *d_table = nullptr, *h_table = nullptr;
+    int *d_replays = nullptr;  // replays since the last table upload
     cudaGraphExec_t exec = nullptr;
     bool composition_changed = true;
     int total_units = 0;
@@ -193,9 +203,8 @@ int setup_shot(sgb_server *sv, Shot *sh)
     a.nrec = sh->nrec;
     a.rec_off = sh->d_off;
     a.traces = sh->d_tr;
-    // A batch already fills the GPU with other shots' units, so each shot takes
-    // the longest z-chunks the single-shot planner allows (32 planes): fewer
-    // priming planes per unit than a plan that must fill the GPU alone.
+    // z-chunks are planned for the whole batch when it is replayed
+    // (plan_chunks); 32 planes until then.
     a.tiles_x = (L.Nx + Cfg::BX - 1) / Cfg::BX;
     a.tiles_y = (L.Ny + Cfg::BY - 1) / Cfg::BY;
     const int chunks = (L.Nz + 31) / 32;
@@ -240,10 +249,44 @@ int retire_shot(sgb_server *sv, Shot *sh)
     return rc;
 }
 
-// Rebuild the device table (and, when the composition changed, the graph).
+// One z-chunk length for every resident shot: the one that minimises waves x
+// (chunk + priming planes) over this GPU's resident-CTA slots for the whole
+// batch.  A lone small shot gets short chunks that fill the GPU; a full batch
+// gets long ones (fewer priming planes).  The arithmetic of a point does not
+// depend on the decomposition, so results do not change.
+void plan_chunks(sgb_server *sv)
+{
+    const long long slots = (long long)sv->ds->sms * sv->ds->occ;
+    int nz_max = 1;
+    for (Shot *sh : sv->resident) nz_max = std::max(nz_max, sh->L.Nz);
+    int best_zc = std::min(32, nz_max);
+    double best = 1e300;
+    for (int zc = std::min(32, nz_max); zc >= 2; --zc) {
+        long long units = 0;
+        for (Shot *sh : sv->resident) {
+            const StepArgs &a = sh->entry.args[0];
+            units += (long long)a.tiles_x * a.tiles_y * ((sh->L.Nz + zc - 1) / zc);
+        }
+        const double cost = (double)((units + slots - 1) / slots) * (zc + 4);
+        if (cost < best * 0.999) {
+            best = cost;
+            best_zc = zc;
+        }
+    }
+    for (Shot *sh : sv->resident) {
+        const int zc = std::min(best_zc, sh->L.Nz);
+        for (int p = 0; p < 2; ++p) sh->entry.args[p].zc = zc;
+        const StepArgs &a = sh->entry.args[0];
+        sh->entry.units = a.tiles_x * a.tiles_y * ((sh->L.Nz + zc - 1) / zc);
+    }
+}
+
+// Rebuild the device table (and, when the composition changed, the chunk plan
+// and the graph).
 int prepare_replay(sgb_server *sv)
 {
     const int ns = (int)sv->resident.size();
+    if (sv->composition_changed || !sv->exec) plan_chunks(sv);
     int units = 0;
     for (int i = 0; i < ns; ++i) {
         Shot *sh = sv->resident[i];
@@ -254,6 +297,7 @@ int prepare_replay(sgb_server *sv)
     }
     CUDA_TRY(cudaMemcpyAsync(sv->d_table, sv->h_table, sizeof(ShotEntry) * ns,
                              cudaMemcpyHostToDevice, sv->stream));
+    CUDA_TRY(cudaMemsetAsync(sv->d_replays, 0, sizeof(int), sv->stream));
     if (!sv->composition_changed && sv->exec) return SGB_OK;
     if (sv->exec) {
         cudaGraphExecDestroy(sv->exec);
@@ -266,7 +310,11 @@ int prepare_replay(sgb_server *sv)
     if (ce == cudaSuccess) {
         for (int i = 0; i < sv->cfg.steps_per_graph && ce == cudaSuccess; ++i) {
             multi_step_kernel<<<units, Cfg::BLOCK, Stage<Cfg, float>::SMEM_BYTES, cs>>>(
-                sv->d_table, ns, i);
+                sv->d_table, ns, i, sv->d_replays, sv->cfg.steps_per_graph);
+            ce = cudaGetLastError();
+        }
+        if (ce == cudaSuccess) {
+            advance_kernel<<<1, 32, 0, cs>>>(sv->d_replays, 1);
             ce = cudaGetLastError();
         }
         cudaError_t ee = cudaStreamEndCapture(cs, &graph);
@@ -305,14 +353,23 @@ void scheduler(sgb_server *sv)
             }
             sv->stats.queued = (int)sv->queue.size();
         }
-        // 1. replay the resident shots (asynchronous)
+        // 1. replay the resident shots (asynchronous), R replays back to back
         int rc = SGB_OK;
         cudaError_t e = cudaSuccess;
         const bool replay = !sv->resident.empty();
+        int R = 1;
+        if (replay && admit.empty()) {
+            int to_finish = MAX_AHEAD_FULL;  // replays until the first resident shot is done
+            for (Shot *sh : sv->resident)
+                to_finish = std::min(to_finish, std::max(1, (sh->nt + 1 - sh->n0 + S - 1) / S));
+            const bool open = (int)sv->resident.size() < sv->cfg.max_slots;
+            R = open ? std::min(to_finish, MAX_AHEAD_OPEN) : to_finish;
+        }
         if (replay) {
             rc = prepare_replay(sv);
-            if (rc == SGB_OK) e = cudaGraphLaunch(sv->exec, sv->stream);
-            t_launches += S;
+            for (int r = 0; r < R && rc == SGB_OK && e == cudaSuccess; ++r)
+                e = cudaGraphLaunch(sv->exec, sv->stream);
+            t_launches += R * (S + 1);
         }
         // 2. meanwhile, set up the admitted shots on the setup stream; they join
         //    at the next replay
@@ -342,7 +399,7 @@ void scheduler(sgb_server *sv)
         std::vector<Shot *> keep, finished;
         if (replay) {
             for (Shot *sh : sv->resident) {
-                sh->n0 += S;
+                sh->n0 += R * S;
                 if (rc != SGB_OK || e != cudaSuccess) sh->status = SGB_ERR_CUDA;
                 if (sh->n0 > sh->nt || sh->status != SGB_OK) finished.push_back(sh);
                 else keep.push_back(sh);
@@ -361,8 +418,8 @@ void scheduler(sgb_server *sv)
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             if (replay) {
-                sv->stats.graph_replays += 1;
-                sv->stats.step_launches += S;
+                sv->stats.graph_replays += R;
+                sv->stats.step_launches += (uint64_t)R * S;
             }
             sv->resident = keep;
             sv->stats.resident = (int)keep.size();
@@ -414,8 +471,11 @@ extern "C" int serve_create(const sgb_serve_config *cfg, sgb_server **out)
         e = cudaMalloc((void **)&sv->d_table, sizeof(ShotEntry) * SERVE_MAX_SLOTS);
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&sv->h_table, sizeof(ShotEntry) * SERVE_MAX_SLOTS);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sv->d_replays, sizeof(int));
     if (e != cudaSuccess) {
         if (sv->d_table) cudaFree(sv->d_table);
+        if (sv->d_replays) cudaFree(sv->d_replays);
+        if (sv->h_table) cudaFreeHost(sv->h_table);
         if (sv->stream) cudaStreamDestroy(sv->stream);
         if (sv->setup_stream) cudaStreamDestroy(sv->setup_stream);
         if (sv->setup_done) cudaEventDestroy(sv->setup_done);
@@ -545,6 +605,7 @@ extern "C" int serve_destroy(sgb_server *sv)
     cudaStreamSynchronize(sv->stream);
     cudaStreamSynchronize(sv->setup_stream);
     cudaFree(sv->d_table);
+    cudaFree(sv->d_replays);
     cudaFreeHost(sv->h_table);
     cudaEventDestroy(sv->setup_done);
     cudaStreamDestroy(sv->setup_stream);
