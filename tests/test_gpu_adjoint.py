@@ -71,3 +71,71 @@ def test_autograd_function():
     assert float(J) == J2
     np.testing.assert_allclose(vt.grad.cpu().numpy(), (3.0 * grad).astype(np.float32), rtol=1e-6,
                                atol=1e-6 * np.abs(3.0 * grad).max())
+
+
+def test_gradient_matches_oracle_several_tiles():
+    """96^3 (64^3 inner + 16-point PML): tile seams in x and y, several z
+    chunks, the PML interface on every face; 120 steps, receivers every 5th
+    surface point, source off the tile grid; observed traces = half those of
+    the model without the anomaly."""
+    n_in, nb, nt = 64, 16, 120
+    N = n_in + 2 * nb
+    shape = (N, N, N)
+    v0 = synth.layered_model(shape, seed=11, vmin=1800, vmax=3200, perturb=0.02)
+    v = (v0 * synth.gaussian_anomaly(shape, (50.0, 45.0, 40.0), 6.0, 0.06)).astype(np.float32)
+    vmax = float(max(v.max(), v0.max()))
+    dt = float(np.float32(0.4 * oracle.cfl_dt(vmax, 10, 10, 10)))
+    wav = synth.ricker(nt, dt, 25.0)
+    src = (nb + 21, nb + 30, nb + 3)
+    rec = synth.surface_receivers(n_in, n_in, nb, 5)
+    go = oracle.Grid(n_in, n_in, n_in, nb, 10.0, 10.0, 10.0, dt, vmax=vmax, r0=float(np.float32(1e-3)))
+    # halved: the anomaly's scattering reaches no receiver in 120 steps, so the
+    # residual against the unperturbed model's own traces would be rounding noise
+    obs = (0.5 * oracle.run_shot(go, v0, wav, nt, src, rec, want_state=False)["traces"]).astype(np.float32)
+    J_ref, grad_ref = oracle.adjoint_shot(go, v, wav, nt, src, rec, obs.astype(np.float64))
+    g = seisgb.make_grid(n_in, n_in, n_in, nb, 10.0, 10.0, 10.0, dt, vmax)
+    grad = np.zeros(shape)
+    J = seisgb.adjoint_shot(g, v, wav, nt, src, rec, obs, grad, ckpt_every=32)
+    e_J, e_g = abs(J - J_ref) / J_ref, rel_l2(grad, grad_ref)
+    print(f"96^3 adjoint vs oracle: misfit {e_J:.3e}, gradient rel L2 {e_g:.3e}")
+    assert e_J <= 1e-4 and e_g <= 1e-3
+
+
+@pytest.mark.slow
+def test_full_size_directional_derivative_and_checkpoints():
+    """The benchmark's gradient case (256^3, 2000 steps, checkpoints every 100),
+    one shot: <dJ/dv, dv> against a central difference of the GPU misfit along
+    the anomaly's own shape (fp32 forward runs, so a loose bound), and the
+    gradient bit-identical with another checkpoint interval."""
+    w = synth.GRADIENT
+    v, v_obs = synth.gradient_models(w)
+    dv = (v - v_obs).astype(np.float64)  # the anomaly: smooth, localised
+    eps = 0.05
+    vmax = float(max(v.max(), v_obs.max(), (v + eps * dv).max()))
+    g0 = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, 1.0, vmax)
+    dt = float(np.float32(w.cfl_fraction * seisgb.cfl_dt(g0, vmax)))
+    g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax)
+    nt = w.nt
+    wav = torch.from_numpy(synth.ricker(nt, dt, w.fp)).cuda()
+    rec = w.receivers()
+    src = synth.shot_grid(w)[5]
+    obs = torch.zeros((nt, rec.shape[0]), device="cuda")
+    seisgb.run_shot(g, torch.from_numpy(v_obs).cuda(), wav, nt, src, rec, obs)
+    d_v = torch.from_numpy(v).cuda()
+    grad = torch.zeros(v.shape, dtype=torch.float64, device="cuda")
+    J = seisgb.adjoint_shot(g, d_v, wav, nt, src, rec, obs, grad, ckpt_every=100)
+    grad2 = torch.zeros_like(grad)
+    J2 = seisgb.adjoint_shot(g, d_v, wav, nt, src, rec, obs, grad2, ckpt_every=64)
+    assert J2 == J and torch.equal(grad, grad2)
+    assert bool(torch.isfinite(grad).all())
+
+    def misfit(vv):
+        tr = torch.zeros((nt, rec.shape[0]), device="cuda")
+        seisgb.run_shot(g, torch.from_numpy(vv.astype(np.float32)).cuda(), wav, nt, src, rec, tr)
+        return 0.5 * float(((tr.double() - obs.double()) ** 2).sum())
+
+    assert abs(misfit(v) - J) <= 1e-6 * J  # the adjoint's misfit is run_shot's
+    fd = (misfit(v + eps * dv) - misfit(v - eps * dv)) / (2 * eps)
+    dd = float((grad * torch.from_numpy(dv).cuda()).sum())
+    print(f"256^3 x 2000: <g, dv> {dd:.6e}, central difference {fd:.6e}, rel {abs(dd - fd) / abs(fd):.2e}")
+    assert abs(dd - fd) <= 2e-2 * abs(fd)
