@@ -246,6 +246,17 @@ int sgb_unpack(const sgb_grid *g, const float *padded, float *compact, void *str
  * Returns SGB_OK, SGB_ERR_TIMEOUT or SGB_ERR_CUDA. */
 int sgb_device_status(void *stream);
 
+/* Self-test of the failure detection the step kernels use (no counterpart in
+ * the paper): launches one kernel whose bounded wait on an mbarrier that
+ * nothing completes -- the wait of a step whose TMA copies never land -- gives
+ * up after limit_us microseconds (1..2,000,000) and sets the timeout bit of the
+ * device error word, which the host then reads and clears as
+ * sgb_device_status does.  *status_out receives that status (SGB_ERR_TIMEOUT
+ * when detection works); the return value is SGB_OK unless the arguments are
+ * invalid or the launch failed.  No GPU fault is involved and the context
+ * stays usable.  Synchronises stream. */
+int sgb_selftest_wait_timeout(int32_t limit_us, int32_t *status_out, void *stream);
+
 /* Number of this library's kernels launched by the calling thread since the
  * last reset (graph replays count every kernel node). */
 int64_t sgb_launch_count(int reset);

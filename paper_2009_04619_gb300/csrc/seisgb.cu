@@ -420,6 +420,43 @@ extern "C" int sgb_unpack(const sgb_grid *g, const float *padded, float *compact
     return SGB_OK;
 }
 
+namespace {
+
+// A bounded wait on an mbarrier that nothing completes, exactly as a step
+// kernel waits for its copies: after limit_ns it gives up and sets the timeout
+// bit of the device error word.
+__global__ void wait_timeout_probe_kernel(int *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(err, DEV_ERR_TIMEOUT);
+}
+
+}  // namespace
+
+extern "C" int sgb_selftest_wait_timeout(int32_t limit_us, int32_t *status_out, void *stream)
+{
+    if (!status_out) return fail(SGB_ERR_INVALID_ARG, "status_out is NULL");
+    if (limit_us < 1 || limit_us > 2000000)
+        return fail(SGB_ERR_INVALID_ARG, "limit_us must be in 1..2000000 (got %d)", limit_us);
+    DevState *ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    if ((rc = read_and_clear_dev_err(*ds, st, &v))) return rc;  // earlier errors are not ours
+    wait_timeout_probe_kernel<<<1, 32, 0, st>>>(ds->err, (unsigned long long)limit_us * 1000ull);
+    CUDA_TRY(cudaGetLastError());
+    ++t_launches;
+    if ((rc = read_and_clear_dev_err(*ds, st, &v))) return rc;
+    *status_out = (v & DEV_ERR_TIMEOUT) ? SGB_ERR_TIMEOUT : v ? SGB_ERR_CUDA : SGB_OK;
+    return SGB_OK;
+}
+
 extern "C" int sgb_device_status(void *stream)
 {
     DevState *ds;

@@ -129,6 +129,8 @@ SIGNATURES = {
     "serve_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServeStats)]),
     "serve_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sgb_device_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "sgb_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                 ctypes.c_void_p]),
     "sgb_launch_count": (ctypes.c_int64, [ctypes.c_int]),
     "sgb_last_error": (ctypes.c_char_p, []),
 }
@@ -268,6 +270,14 @@ def unpack(g: Grid, padded, compact, stream=None):
 
 def device_status(stream=None):
     _check(lib().sgb_device_status(_stream(stream)))
+
+
+def selftest_wait_timeout(limit_us: int, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status the host read from the
+    device error word (ERR_TIMEOUT when failure detection works)."""
+    st = ctypes.c_int32(0)
+    _check(lib().sgb_selftest_wait_timeout(int(limit_us), ctypes.byref(st), _stream(stream)))
+    return int(st.value)
 
 
 def launch_count(reset: bool = False) -> int:

@@ -147,3 +147,11 @@ def test_serve_config_rejected_without_gpu(lib, budget, slots, steps):
     cfg = seisgb.ServeConfig(budget, slots, steps)
     h = ctypes.c_void_p()
     assert seisgb.lib().serve_create(ctypes.byref(cfg), ctypes.byref(h)) == seisgb.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("limit_us", [0, -5, 2000001])
+def test_wait_selftest_arguments_checked_without_gpu(lib, limit_us):
+    st = ctypes.c_int32(7)
+    assert lib.sgb_selftest_wait_timeout(limit_us, ctypes.byref(st), None) == seisgb.ERR_INVALID_ARG
+    assert st.value == 7
+    assert lib.sgb_selftest_wait_timeout(1000, None, None) == seisgb.ERR_INVALID_ARG
