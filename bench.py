@@ -428,6 +428,23 @@ def main():
     ms_per_step = ms / a.steps
     value = replicas.job_rate(w.points * w.nt * a.steps, ms / 1e3, world) / 1e9
 
+    # end to end through the C ABI with pinned host buffers, right after the
+    # device-resident timing (same GPU state): velocity and wavelet
+    # copied in, traces copied out, every step
+    h_v = torch.from_numpy(vel).pin_memory()
+    h_w = torch.from_numpy(wav).pin_memory()
+    h_tr = torch.zeros((w.nt, nrec), dtype=torch.float32).pin_memory()
+    seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
+    barrier()
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t, device=dev)
+    e2e_val = replicas.job_rate(w.points * w.nt * a.steps, e2e_s, world) / 1e9
+    h2d = vel.nbytes + wav.nbytes + rec.nbytes + 12
+    d2h = w.nt * nrec * 4
+
     # dominant kernel: back-to-back fused steps on the same grid, CUDA events on
     # the launching stream
     L = seisgb.layout(g)
@@ -475,22 +492,6 @@ def main():
 
     serving = _serving(a, seisgb, synth, value) if a.serve_requests > 0 else None
     gradient = _gradient(a, seisgb, synth, peak) if a.grad_shots > 0 else None
-
-    # end to end through the C ABI with pinned host buffers: velocity and wavelet
-    # copied in, traces copied out, every step
-    h_v = torch.from_numpy(vel).pin_memory()
-    h_w = torch.from_numpy(wav).pin_memory()
-    h_tr = torch.zeros((w.nt, nrec), dtype=torch.float32).pin_memory()
-    seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
-    barrier()
-    t = time.perf_counter()
-    for _ in range(a.steps):
-        seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
-    barrier()
-    e2e_s = replicas.max_over_ranks(time.perf_counter() - t, device=dev)
-    e2e_val = replicas.job_rate(w.points * w.nt * a.steps, e2e_s, world) / 1e9
-    h2d = vel.nbytes + wav.nbytes + rec.nbytes + 12
-    d2h = w.nt * nrec * 4
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
