@@ -94,18 +94,6 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     return p;
 }
 
-__device__ __forceinline__ uint64_t policy_evict_last()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
-{
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-
 // Approximate reciprocal (the PTX rcp.approx instruction, about 1 ulp); used
 // for 1 / (1 + eta dt), whose argument lies in [1, 2].
 __device__ __forceinline__ float rcp_approx(float x)
@@ -131,14 +119,6 @@ __device__ __forceinline__ void stg128(float *p, float4 v)
 {
     asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
                  "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
-// 128-bit global store with an L2 cache-policy hint.
-__device__ __forceinline__ void stg128_hint(float *p, float4 v, uint64_t policy)
-{
-    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x),
-                 "f"(v.y), "f"(v.z), "f"(v.w), "l"(policy)
                  : "memory");
 }
 

@@ -185,6 +185,40 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _desc(x):
+    """(dtype name, C-contiguous, element count, on a CUDA device) of a numpy
+    array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        return x.dtype.name, bool(x.flags.c_contiguous), int(x.size), False
+    return (str(x.dtype).replace("torch.", ""), bool(x.is_contiguous()), int(x.numel()),
+            bool(x.is_cuda))
+
+
+def _buf(x, name: str, dtype: str, min_numel: int, optional: bool = False, cuda: bool = False):
+    """Address of `x` after checking what the C side cannot: element type,
+    C-contiguity, at least `min_numel` elements, and (cuda=True) that it lives
+    on the GPU.  Raises ValueError otherwise."""
+    if x is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    dt, contiguous, numel, on_cuda = _desc(x)
+    if dt != dtype:
+        raise ValueError(f"{name}: expected {dtype} elements, got {dt}")
+    if not contiguous:
+        raise ValueError(f"{name} must be contiguous")
+    if numel < min_numel:
+        raise ValueError(f"{name}: {numel} elements, at least {min_numel} needed")
+    if cuda and not on_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return _ptr(x)
+
+
+def _points(g: Grid) -> int:
+    a, b, c = g.shape
+    return a * b * c
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -199,17 +233,21 @@ def stencil_step(g: Grid, u_cur, u_prev_to_next, m, phi, step: int = 0, source=N
     """One fused step.  Fields: CUDA tensors in the padded layout.
     source: (i, j, k, wavelet_cuda_tensor) or None.
     receivers: (ijk int32 numpy [nrec, 3], traces_row cuda tensor [nrec]) or None."""
+    E = int(layout(g).elems)
     src = None
     if source is not None:
         i, j, k, w = source
-        src = Source(int(i), int(j), int(k), _ptr(w))
+        src = Source(int(i), int(j), int(k), _buf(w, "wavelet", "float32", int(step) + 1, cuda=True))
     rec = None
     keep = None
     if receivers is not None:
         ijk, row = receivers
         keep = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
-        rec = Receivers(keep.shape[0], keep.ctypes.data, _ptr(row))
-    rc = lib().stencil_step(ctypes.byref(g), _ptr(u_cur), _ptr(u_prev_to_next), _ptr(m), _ptr(phi),
+        rec = Receivers(keep.shape[0], keep.ctypes.data,
+                        _buf(row, "traces row", "float32", keep.shape[0], cuda=True))
+    fields = [_buf(f, nm, "float32", E, cuda=True)
+              for f, nm in ((u_cur, "u_cur"), (u_prev_to_next, "u_prev_to_next"), (m, "m"))]
+    rc = lib().stencil_step(ctypes.byref(g), *fields, _buf(phi, "phi", "float32", E, cuda=True),
                             int(step), ctypes.byref(src) if src is not None else None,
                             ctypes.byref(rec) if rec is not None else None, _stream(stream))
     del keep
@@ -223,10 +261,13 @@ def run_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, traces, fina
     s = None if src_ijk is None else np.ascontiguousarray(np.asarray(src_ijk, dtype=np.int32))
     r = np.ascontiguousarray(np.asarray(rec_ijk, dtype=np.int32).reshape(-1, 3))
     nrec = r.shape[0]
-    _check(lib().run_shot(ctypes.byref(g), _ptr(velocity), _ptr(wavelet), int(nt),
+    N, nt = _points(g), int(nt)
+    _check(lib().run_shot(ctypes.byref(g), _buf(velocity, "velocity", "float32", N),
+                          _buf(wavelet, "wavelet", "float32", nt, optional=s is None), nt,
                           None if s is None else s.ctypes.data,
                           r.ctypes.data if nrec else None, nrec,
-                          _ptr(traces) if nrec else None, _ptr(final_u), _stream(stream)))
+                          _buf(traces, "traces", "float32", nt * nrec) if nrec else None,
+                          _buf(final_u, "final_u", "float32", N, optional=True), _stream(stream)))
 
 
 def adjoint_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, observed, grad_velocity,
@@ -237,10 +278,13 @@ def adjoint_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, observed
     s = np.ascontiguousarray(np.asarray(src_ijk, dtype=np.int32))
     r = np.ascontiguousarray(np.asarray(rec_ijk, dtype=np.int32).reshape(-1, 3))
     J = ctypes.c_double()
-    _check(lib().adjoint_shot(ctypes.byref(g), _ptr(velocity), _ptr(wavelet), int(nt),
-                              s.ctypes.data, r.ctypes.data, r.shape[0], _ptr(observed),
-                              int(ckpt_every), ctypes.byref(J), _ptr(grad_velocity),
-                              _stream(stream)))
+    N, nt, nrec = _points(g), int(nt), r.shape[0]
+    _check(lib().adjoint_shot(ctypes.byref(g), _buf(velocity, "velocity", "float32", N),
+                              _buf(wavelet, "wavelet", "float32", nt), nt,
+                              s.ctypes.data, r.ctypes.data, nrec,
+                              _buf(observed, "observed", "float32", nt * nrec),
+                              int(ckpt_every), ctypes.byref(J),
+                              _buf(grad_velocity, "grad_velocity", "float64", N), _stream(stream)))
     return J.value
 
 
@@ -253,19 +297,27 @@ def run_shot_noalloc(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, trac
     s = None if src_ijk is None else np.ascontiguousarray(np.asarray(src_ijk, dtype=np.int32))
     r = np.ascontiguousarray(np.asarray(rec_ijk, dtype=np.int32).reshape(-1, 3))
     nrec = r.shape[0]
-    _check(lib().run_shot_noalloc(ctypes.byref(g), _ptr(velocity), _ptr(wavelet), int(nt),
-                                  None if s is None else s.ctypes.data,
+    N, nt = _points(g), int(nt)
+    _check(lib().run_shot_noalloc(ctypes.byref(g), _buf(velocity, "velocity", "float32", N),
+                                  _buf(wavelet, "wavelet", "float32", nt, optional=s is None),
+                                  nt, None if s is None else s.ctypes.data,
                                   r.ctypes.data if nrec else None, nrec,
-                                  _ptr(traces) if nrec else None, _ptr(final_u),
+                                  _buf(traces, "traces", "float32", nt * nrec) if nrec else None,
+                                  _buf(final_u, "final_u", "float32", N, optional=True),
                                   _stream(stream)))
 
 
 def pack(g: Grid, compact, padded, stream=None):
-    _check(lib().sgb_pack(ctypes.byref(g), _ptr(compact), _ptr(padded), _stream(stream)))
+    E = int(layout(g).elems)
+    _check(lib().sgb_pack(ctypes.byref(g), _buf(compact, "compact", "float32", _points(g), cuda=True),
+                          _buf(padded, "padded", "float32", E, cuda=True), _stream(stream)))
 
 
 def unpack(g: Grid, padded, compact, stream=None):
-    _check(lib().sgb_unpack(ctypes.byref(g), _ptr(padded), _ptr(compact), _stream(stream)))
+    E = int(layout(g).elems)
+    _check(lib().sgb_unpack(ctypes.byref(g), _buf(padded, "padded", "float32", E, cuda=True),
+                            _buf(compact, "compact", "float32", _points(g), cuda=True),
+                            _stream(stream)))
 
 
 def device_status(stream=None):

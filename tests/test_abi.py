@@ -155,3 +155,32 @@ def test_wait_selftest_arguments_checked_without_gpu(lib, limit_us):
     assert lib.sgb_selftest_wait_timeout(limit_us, ctypes.byref(st), None) == seisgb.ERR_INVALID_ARG
     assert st.value == 7
     assert lib.sgb_selftest_wait_timeout(1000, None, None) == seisgb.ERR_INVALID_ARG
+
+
+def test_binding_checks_buffers_before_the_c_call(lib):
+    """Element type, contiguity, size and (for device-only calls) residency are
+    checked in Python: the C ABI takes plain pointers and cannot."""
+    g = seisgb.make_grid(8, 8, 8, 2, 10.0, 10.0, 10.0, 1e-3, 2000.0)
+    N = int(np.prod(g.shape))
+    nt, rec = 4, np.array([[4, 4, 2]], dtype=np.int32)
+    v = np.full(g.shape, 2000.0, dtype=np.float32)
+    w = np.zeros(nt, dtype=np.float32)
+    tr = np.zeros((nt, 1), dtype=np.float32)
+    with pytest.raises(ValueError, match="float32"):
+        seisgb.run_shot(g, v.astype(np.float64), w, nt, (4, 4, 4), rec, tr)
+    with pytest.raises(ValueError, match="at least"):
+        seisgb.run_shot(g, v.ravel()[:N - 1], w, nt, (4, 4, 4), rec, tr)
+    with pytest.raises(ValueError, match="contiguous"):
+        seisgb.run_shot(g, np.asfortranarray(v), w, nt, (4, 4, 4), rec, tr)
+    with pytest.raises(ValueError, match="at least"):
+        seisgb.run_shot(g, v, w[:2], nt, (4, 4, 4), rec, tr)
+    with pytest.raises(ValueError, match="at least"):
+        seisgb.run_shot(g, v, w, nt, (4, 4, 4), rec, tr[:2])
+    with pytest.raises(ValueError, match="float64"):
+        seisgb.adjoint_shot(g, v, w, nt, (4, 4, 4), rec, tr, np.zeros(g.shape, np.float32))
+    E = int(seisgb.layout(g).elems)
+    f = np.zeros(E, dtype=np.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        seisgb.stencil_step(g, f, f.copy(), f.copy(), f.copy(), 0)
+    with pytest.raises(ValueError, match="CUDA"):
+        seisgb.pack(g, v, f)
