@@ -3,10 +3,13 @@ time per launch (CUDA events) -- a small driver for timing and for ncu captures.
 
     python -m paper_2009_04619_gb300.profile_step --n 256 --nb 32 --launches 20
     python -m paper_2009_04619_gb300.profile_step --adjoint --n 256 --nb 16 --nt 200
+    python -m paper_2009_04619_gb300.profile_step --storage fp16 --n 512 --nb 32 --nt 40
 
 With --adjoint it runs one misfit-gradient shot instead (layered model with a
 Gaussian anomaly, observed traces from the model without it) and reports its
-time beside a forward shot of the same length.
+time beside a forward shot of the same length.  With --storage fp16 or bf16 it
+runs a short run_shot with 16-bit wavefield storage (fp32 arithmetic) and
+reports the time per step.
 """
 from __future__ import annotations
 
@@ -52,6 +55,32 @@ def _adjoint(a):
                       "grad_finite": bool(torch.isfinite(grad).all())}))
 
 
+def _storage(a):
+    n_in = a.n - 2 * a.nb
+    v = 3000.0
+    fmt = {"fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
+    g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, 1.0, v)
+    dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, v)))
+    g = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, dt, v, storage=fmt)
+    vel = torch.full(g.shape, v, device="cuda")
+    wav = torch.from_numpy(synth.ricker(a.nt, dt, 10.0)).cuda()
+    src = (a.n // 2, a.n // 2, a.n // 2)
+    rec = synth.surface_receivers(n_in, n_in, a.nb, 8)
+    tr = torch.zeros((a.nt, rec.shape[0]), device="cuda")
+    seisgb.run_shot(g, vel, wav, a.nt, src, rec, tr)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    seisgb.run_shot(g, vel, wav, a.nt, src, rec, tr)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.nt
+    pts = a.n ** 3
+    alg = 10 * pts + 8 * (pts - n_in ** 3)  # 2 B wavefields (3 x), 4 B m, phi at PML points
+    print(json.dumps({"n": a.n, "nb": a.nb, "storage": a.storage, "nt": a.nt, "ms_per_step": ms,
+                      "gpts": pts / ms / 1e6, "alg_gbs": alg / ms / 1e6}))
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--n", type=int, default=256, help="computed points per axis")
@@ -62,6 +91,8 @@ def main(argv=None):
     p.add_argument("--adjoint", action="store_true", help="time one misfit-gradient shot")
     p.add_argument("--nt", type=int, default=200, help="time steps of the gradient shot")
     p.add_argument("--ckpt", type=int, default=100, help="checkpoint interval of the gradient shot")
+    p.add_argument("--storage", choices=["fp16", "bf16"], default=None,
+                   help="time a short run_shot with 16-bit wavefield storage")
     a = p.parse_args(argv)
     if a.lib:
         seisgb.LIB_PATH = a.lib
@@ -69,6 +100,9 @@ def main(argv=None):
         build.build()
     if a.adjoint:
         _adjoint(a)
+        return
+    if a.storage:
+        _storage(a)
         return
     n_in = a.n - 2 * a.nb  # nb = 0: no PML, every tile takes the interior path
     h, v = 10.0, 4500.0
