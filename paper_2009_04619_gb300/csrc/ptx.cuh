@@ -94,6 +94,13 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     return p;
 }
 
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Approximate reciprocal (the PTX rcp.approx instruction, about 1 ulp); used
 // for 1 / (1 + eta dt), whose argument lies in [1, 2].
 __device__ __forceinline__ float rcp_approx(float x)

@@ -288,7 +288,7 @@ int encode_step_maps(StepMaps &mp, const void *u_cur, const void *u_prev, const 
     if ((rc = encode_map<T>(&mp.ucur_in, u_cur, L, Cfg::BX, Cfg::BY))) return rc;
     if ((rc = encode_map<T>(&mp.uprev, u_prev, L, Cfg::BX, Cfg::BY))) return rc;
     if ((rc = encode_map<float>(&mp.m, m, L, Cfg::BX, Cfg::BY))) return rc;
-    if ((rc = encode_map<float>(&mp.phi, phi ? phi : m, L, Cfg::BX, Cfg::BY))) return rc;
+    if ((rc = encode_map<float>(&mp.phi, phi ? phi : m, L, Cfg::PHI_BW, Cfg::BY))) return rc;
     return SGB_OK;
 }
 

@@ -237,7 +237,12 @@ struct TileCfg {
     static constexpr int SH = BY + 2 * R;
     static constexpr int P_TILE = BX * BY;
     static constexpr int WARPS = THREADS / 32;
+    // phi (or mu) tiles travel as PHI_BW-column blocks, stored block after
+    // block in shared memory, so that a tile touching only the x-PML can load
+    // just the blocks that hold PML columns
+    static constexpr int PHI_BW = 32, PHI_NB = BX / PHI_BW;
     static_assert(NU >= 8, "the u ring must hold the 8 planes that prime the register queue");
+    static_assert(BX % PHI_BW == 0 && PHI_NB <= 8, "phi blocks");
     static_assert(U_ >= 1 && U_ <= 9, "unroll factor");
     static_assert(NP >= 2 && THREADS % 32 == 0, "ring sizes");
     static_assert(SH <= 256 && BX <= 240 && BY <= 256, "TMA box limits");
@@ -335,6 +340,9 @@ struct StepCta {
     long long base_off;  // element offset of (gi, gj0, k = 0)
     int tid, lane, x0, y0, z0, z1, n, row0, colu, gi, gj0, prow;
     bool xy_inner, aborted, store_ok;
+    int phi_xmask;  // phi blocks holding x-PML columns, when the tile touches only the
+                    // x-PML (planes outside the z-PML load only these); 0 otherwise
+    int phoff;      // offset of this thread's row-0 quad in the blocked phi tile
     float s_cur, s_prev, inv_s_next;  // fp16 scales (1 otherwise)
     float vmax;                       // running max |u^{n+1}| of this thread
     // PML terms of the thread's fixed columns i = gi + e and rows j = gj0 + r:
@@ -423,7 +431,9 @@ struct StepCta {
         lastf_u[s] = f;
         if (front_only(p)) {
             mbar_arrive_expect_tx(full_u + s, P_TILE * (int)sizeof(T));
-            tma_load_3d(su + s * G::U_BYTES, tm_ucur_in, full_u + s, x0, y0, p);
+            // a neighbouring z-chunk's plane: kept in L2 for that chunk's own read
+            tma_load_3d_hint(su + s * G::U_BYTES, tm_ucur_in, full_u + s, x0, y0, p,
+                             policy_evict_last());
         } else {
             mbar_arrive_expect_tx(full_u + s, SW * C::SH * (int)sizeof(T));
             tma_load_3d(su + s * G::U_BYTES, tm_ucur, full_u + s, x0 - HX, y0 - R, p);
@@ -437,13 +447,21 @@ struct StepCta {
         if (f > 0) wait(empty_p + s, (f - 1) & 1);
         lastf_p[s] = f;
         const bool pml = plane_pml(k);
-        const int ntiles = (pml ? 2 : 1) + (MODE == MODE_ADJ ? 2 : 0);
-        mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + ntiles * G::F_BYTES);
+        const bool zpml = k < pa->nb || k >= pa->nb + pa->nz;
+        const int phmask = !pml ? 0 : (phi_xmask && !zpml) ? phi_xmask : (1 << C::PHI_NB) - 1;
+        const int ntiles = 1 + (MODE == MODE_ADJ ? 2 : 0);
+        constexpr int PHB_BYTES = C::PHI_BW * C::BY * 4;
+        mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + ntiles * G::F_BYTES +
+                                              __popc(phmask) * PHB_BYTES);
         unsigned char *d = sp + s * G::P_BYTES;
         const uint64_t pol = policy_evict_first();
         tma_load_3d_hint(d, tm_uprev, full_p + s, x0, y0, k, pol);
         tma_load_3d_hint(d + G::UP_BYTES, tm_m, full_p + s, x0, y0, k, pol);
-        if (pml) tma_load_3d_hint(d + G::UP_BYTES + G::F_BYTES, tm_phi, full_p + s, x0, y0, k, pol);
+#pragma unroll
+        for (int b = 0; b < C::PHI_NB; ++b)
+            if ((phmask >> b) & 1)
+                tma_load_3d_hint(d + G::UP_BYTES + G::F_BYTES + b * PHB_BYTES, tm_phi, full_p + s,
+                                 x0 + b * C::PHI_BW, y0, k, pol);
         if constexpr (MODE == MODE_ADJ) {  // g^{k-1} of the recomputation; partial sum S
             tma_load_3d_hint(d + G::UP_BYTES + 2 * G::F_BYTES, tm_acc, full_p + s, x0, y0, k, pol);
             tma_load_3d_hint(d + G::UP_BYTES + 3 * G::F_BYTES, tm_gs, full_p + s, x0, y0, k, pol);
@@ -567,7 +585,7 @@ struct StepCta {
             int ptmask = 0;
             float4 ph = make_float4(0.f, 0.f, 0.f, 0.f);
             if (PML) {
-                ph = lds128(pph + pr);
+                ph = lds128(pph + phoff + r * C::PHI_BW);
                 phn = ph;
                 const float eyz = ZP ? __fadd_rn(pey[r], ez) : 0.0f;
                 const float gyk = pgy[r];
@@ -839,6 +857,14 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     const int xe = min(st.x0 + BX, a.Nx), ye = min(st.y0 + BY, a.Ny);
     st.xy_inner = st.x0 >= a.nb + S::BAND && xe <= a.nb + a.nx - S::BAND &&
                   st.y0 >= a.nb + S::BAND && ye <= a.nb + a.ny - S::BAND;
+    st.phi_xmask = 0;
+    if (MODE != MODE_ADJ && !st.xy_inner && st.y0 >= a.nb && ye <= a.nb + a.ny) {
+        // rows all y-inner: only columns in the x-PML need phi outside the z-PML
+        for (int b = 0; b < C::PHI_NB; ++b) {
+            const int c0 = st.x0 + b * C::PHI_BW, c1 = min(c0 + C::PHI_BW, a.Nx);
+            if (c0 < a.Nx && (c0 < a.nb || c1 > a.nb + a.nx)) st.phi_xmask |= 1 << b;
+        }
+    }
 
     if (tid == THREADS) {
         *st.s_abort = 0;
@@ -868,6 +894,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     st.gi = st.x0 + 4 * txi;
     st.gj0 = st.y0 + TY * tyi;
     st.prow = (TY * tyi) * BX + 4 * txi;
+    st.phoff = (4 * txi / C::PHI_BW) * C::PHI_BW * BY + (TY * tyi) * C::PHI_BW + (4 * txi) % C::PHI_BW;
     st.store_ok = st.gi < a.Nx;
     st.base_off = a.origin + (long long)st.gj0 * a.sx + st.gi;
     st.pml_tables();
