@@ -213,6 +213,11 @@ typedef struct {
     int32_t resident, queued;
     uint64_t graph_replays, step_launches;
     uint64_t device_bytes;      /* bytes held by resident shots */
+    /* scheduler-thread time (ms, cumulative): setting up admitted shots (host
+     * side; their copies overlap the running replays), uploading the shot
+     * table and re-capturing the replay graph, retiring finished shots, and
+     * waiting for enqueued replays to finish */
+    double setup_ms, prepare_ms, retire_ms, wait_ms;
 } sgb_serve_stats;
 
 typedef struct sgb_server sgb_server;

@@ -365,12 +365,16 @@ void scheduler(sgb_server *sv)
             const bool open = (int)sv->resident.size() < sv->cfg.max_slots;
             R = open ? std::min(to_finish, MAX_AHEAD_OPEN) : to_finish;
         }
+        Clock::time_point tp = Clock::now();
+        double t_prep = 0.0, t_setup = 0.0, t_wait = 0.0, t_retire = 0.0;
         if (replay) {
             rc = prepare_replay(sv);
+            t_prep = ms_between(tp, Clock::now());
             for (int r = 0; r < R && rc == SGB_OK && e == cudaSuccess; ++r)
                 e = cudaGraphLaunch(sv->exec, sv->stream);
             t_launches += R * (S + 1);
         }
+        tp = Clock::now();
         // 2. meanwhile, set up the admitted shots on the setup stream; they join
         //    at the next replay
         std::vector<Shot *> joined;
@@ -394,8 +398,12 @@ void scheduler(sgb_server *sv)
             cudaEventRecord(sv->setup_done, sv->setup_stream);
             cudaStreamWaitEvent(sv->stream, sv->setup_done, 0);
         }
+        t_setup = ms_between(tp, Clock::now());
+        tp = Clock::now();
         // 3. wait for the replay, advance and retire
         if (replay && e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
+        t_wait = ms_between(tp, Clock::now());
+        tp = Clock::now();
         std::vector<Shot *> keep, finished;
         if (replay) {
             for (Shot *sh : sv->resident) {
@@ -415,12 +423,17 @@ void scheduler(sgb_server *sv)
         }
         for (Shot *sh : joined) keep.push_back(sh);
         if (!finished.empty() || !joined.empty()) sv->composition_changed = true;
+        t_retire = ms_between(tp, Clock::now());
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             if (replay) {
                 sv->stats.graph_replays += R;
                 sv->stats.step_launches += (uint64_t)R * S;
             }
+            sv->stats.prepare_ms += t_prep;
+            sv->stats.setup_ms += t_setup;
+            sv->stats.wait_ms += t_wait;
+            sv->stats.retire_ms += t_retire;
             sv->resident = keep;
             sv->stats.resident = (int)keep.size();
             for (Shot *sh : finished) {

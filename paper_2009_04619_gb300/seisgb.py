@@ -89,7 +89,9 @@ class ServeStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("rejected", ctypes.c_uint64), ("resident", ctypes.c_int32),
                 ("queued", ctypes.c_int32), ("graph_replays", ctypes.c_uint64),
-                ("step_launches", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+                ("step_launches", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("setup_ms", ctypes.c_double), ("prepare_ms", ctypes.c_double),
+                ("retire_ms", ctypes.c_double), ("wait_ms", ctypes.c_double)]
 
 
 _lib = None
