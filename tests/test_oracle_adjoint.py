@@ -89,3 +89,43 @@ def test_gradient_vs_central_differences_single_points(where):
     fd = (jp - jm) / 2.0
     ad = float(grad[k, j, i] * dv[k, j, i])
     assert abs(fd - ad) <= 1e-3 * abs(fd), (where, (i, j, k), fd, ad)
+
+
+def test_gradient_vs_central_differences_anisotropic_ragged():
+    """Unequal spacings and extents (a swapped axis or spacing in the adjoint's
+    PML terms would show here): inner 9 x 7 x 6, 5-point PML, dx, dy, dz =
+    10, 13, 8 m, 40 steps; random directions and the most sensitive PML point
+    on each axis."""
+    nx, ny, nz, nb, nt = 9, 7, 6, 5, 40
+    dxs = (10.0, 13.0, 8.0)
+    shape = (nz + 2 * nb, ny + 2 * nb, nx + 2 * nb)
+    v0 = synth.layered_model(shape, seed=8, vmin=1800, vmax=2800, perturb=0.0)
+    v = (v0 * synth.gaussian_anomaly(shape, (9.0, 8.0, 8.0), 2.0, 0.1)).astype(np.float32)
+    vmax = float(max(v.max(), v0.max()))
+    dt = float(np.float32(0.4 * oracle.cfl_dt(vmax, *dxs)))
+    g = oracle.Grid(nx, ny, nz, nb, *dxs, dt, vmax=vmax, r0=1e-3)
+    wav = synth.ricker(nt, dt, 45.0)
+    src = (nb + 1, nb + 5, nb + 1)
+    rec = np.array([[nb + i, nb + j, nb] for j in range(0, ny, 2) for i in range(0, nx, 2)],
+                   dtype=np.int32)
+    obs = 0.5 * oracle.run_shot(g, v0, wav, nt, src, rec, want_state=False)["traces"]
+    J, grad = oracle.adjoint_shot(g, v, wav, nt, src, rec, obs)
+    rng = np.random.default_rng(2)
+    for _ in range(2):
+        dv = (rng.integers(-2, 3, size=v.shape) * EXACT).astype(np.float32)
+        fd = (_misfit(g, (v + dv).astype(np.float32), wav, nt, src, rec, obs) -
+              _misfit(g, (v - dv).astype(np.float32), wav, nt, src, rec, obs)) / 2.0
+        assert abs(fd - float(np.sum(grad * dv))) <= 1e-3 * abs(fd)
+    # the most sensitive point in the x-only, y-only and z-only PML
+    Nz, Ny, Nx = shape
+    K, Jj, I = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+    depth = lambda q, n: np.maximum(np.maximum(nb - q, q - (nb + n - 1)), 0)
+    ddx, ddy, ddz = depth(I, nx), depth(Jj, ny), depth(K, nz)
+    for mask in ((ddx > 0) & (ddy == 0) & (ddz == 0), (ddy > 0) & (ddx == 0) & (ddz == 0),
+                 (ddz > 0) & (ddx == 0) & (ddy == 0)):
+        idx = np.unravel_index(np.argmax(np.where(mask, np.abs(grad), -1.0)), shape)
+        dv = np.zeros(shape, np.float32)
+        dv[idx] = 4 * EXACT
+        fd = (_misfit(g, (v + dv).astype(np.float32), wav, nt, src, rec, obs) -
+              _misfit(g, (v - dv).astype(np.float32), wav, nt, src, rec, obs)) / 2.0
+        assert abs(fd - float(np.sum(grad * dv))) <= 1e-3 * abs(fd), (idx, fd)
