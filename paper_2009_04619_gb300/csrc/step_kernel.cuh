@@ -21,8 +21,12 @@
 //  - planes of u^n arrive by TMA, with their radius-4 x-y halo, into an
 //    NU-stage shared-memory ring (the 4 planes below and above a z-chunk are
 //    only needed for the z-neighbours of the chunk's own points, so they come
-//    without the halo); u^{n-1}, m and (PML planes only) phi tiles
-//    into an NP-stage ring; one lane of a dedicated producer warp issues the
+//    without the halo, with an L2 evict-last hint for the neighbouring chunk
+//    that reads them again); u^{n-1}, m and (PML planes only) phi tiles
+//    into an NP-stage ring, with no evict-first hint because u^{n-1} and phi
+//    are rewritten in place a few planes later; phi comes in 32-column blocks,
+//    and a tile that touches only the x-PML loads only the blocks holding PML
+//    columns outside the z-PML; one lane of a dedicated producer warp issues the
 //    copies in the order the consumers need them, as far ahead as the rings
 //    allow; "full" mbarriers carry copy completion to the consumer warps and
 //    "empty" mbarriers (one arrival per consumer warp) carry slot release back
@@ -36,10 +40,11 @@
 //    its code no longer fits the instruction cache;
 //  - whether a plane takes the PML path depends only on the tile and k, so
 //    the branch is uniform across the CTA: the z range of a tile splits into
-//    PML and interior segments, each a separately compiled loop, which keeps
-//    the hot interior loop small enough for the instruction cache; inside a
-//    PML-path plane, inner points select the Eq. 2 result computed by the same
-//    instructions as the interior path, bit for bit;
+//    segments of three plane kinds (interior; PML path outside the z-PML, where
+//    1/(1+e) and 1-e come from per-thread tables; z-PML), each a separately
+//    compiled loop, which keeps the hot interior loop small enough for the
+//    instruction cache; inside a PML-path plane, inner points select the Eq. 2
+//    result computed by the same instructions as the interior path, bit for bit;
 //  - eta and its central differences are evaluated in closed form from the
 //    integer depth into the layer: no eta array is read;
 //  - every mbarrier wait is bounded (2 s); on timeout the CTA records
