@@ -126,17 +126,25 @@ __device__ __forceinline__ uint32_t hash_bits(uint32_t a, uint32_t b)
     return h;
 }
 
-// Stochastic rounding of x to a format that keeps the top (32 - drop) bits of
-// the fp32 pattern: add random bits below the kept ones, then truncate.  With
-// round-to-nearest, the rounding errors of a smooth field repeat from step to
-// step and add up coherently over a run; stochastic rounding makes them
-// uncorrelated (zero mean), so they grow like a random walk instead.
-template <int DROP>
-__device__ __forceinline__ float sr_bits(float x, uint32_t rnd)
+// Stochastic rounding of an fp32 pair to 16 bits in the conversion itself
+// (the cvt.rs form of sm_100-family GPUs, fed 32 random bits): each value
+// rounds up with probability equal to its distance from the lower neighbour.
+// With round-to-nearest, the rounding errors of a smooth field repeat from
+// step to step and add up coherently over a run; stochastic rounding makes
+// them uncorrelated (zero mean), so they grow like a random walk instead.
+// The first source operand of the pair conversion lands in the upper half.
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float lo, float hi, uint32_t rnd)
 {
-    const uint32_t b = __float_as_uint(x);
-    if ((b & 0x7F800000u) == 0x7F800000u) return x;  // Inf / NaN unchanged
-    return __uint_as_float(b + (rnd & ((1u << DROP) - 1u)));
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rnd));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float lo, float hi, uint32_t rnd)
+{
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rnd));
+    return d;
 }
 
 // Storage traits: TMA x margin (16 bytes), 4-wide loads from shared memory and
@@ -172,9 +180,8 @@ struct Elem<__half> {
         (void)rnd;
         return __floats2half2_rn(x, y);
 #else
-        // fp16 keeps 10 of fp32's 23 mantissa bits (normal range): drop 13
-        return __halves2half2(__float2half_rz(sr_bits<13>(x, rnd)),
-                              __float2half_rz(sr_bits<13>(y, rnd >> 13)));
+        const uint32_t d = cvt_rs_f16x2(x, y, rnd);
+        return *reinterpret_cast<const __half2 *>(&d);
 #endif
     }
     __device__ static __forceinline__ void st(__half *p, float4 v, uint32_t rnd)
@@ -209,9 +216,8 @@ struct Elem<__nv_bfloat16> {
         (void)rnd;
         return __floats2bfloat162_rn(x, y);
 #else
-        // bf16 is the top 16 bits of fp32: drop 16
-        return __halves2bfloat162(__float2bfloat16_rz(sr_bits<16>(x, rnd)),
-                                  __float2bfloat16_rz(sr_bits<16>(y, rnd >> 16)));
+        const uint32_t d = cvt_rs_bf16x2(x, y, rnd);
+        return *reinterpret_cast<const __nv_bfloat162 *>(&d);
 #endif
     }
     __device__ static __forceinline__ void st(__nv_bfloat16 *p, float4 v, uint32_t rnd)
