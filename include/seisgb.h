@@ -236,6 +236,8 @@ int serve_submit(sgb_server *s, const sgb_shot_request *req, uint64_t *ticket);
  * is then forgotten).  SGB_PENDING: not done and timeout_us == 0.
  * SGB_ERR_TIMEOUT: not done within timeout_us (> 0).  INVALID_ARG: unknown. */
 int serve_poll(sgb_server *s, uint64_t ticket, sgb_shot_result *out, int32_t timeout_us);
+/* Copy of the server's counters (taken under the server's lock, so the fields
+ * are consistent with each other); INVALID_ARG if s or out is NULL. */
 int serve_stats(sgb_server *s, sgb_serve_stats *out);
 /* Cancel queued requests, finish resident shots, stop the scheduler, free all
  * device memory. */
