@@ -139,6 +139,9 @@ int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int
  *   observed  nt*nrec fp32 (same layout as run_shot's traces), host or device
  *   misfit_out     host double
  *   grad_velocity  Nz*Ny*Nx fp64 compact, host or device
+ * Calls on different streams (e.g. one host thread per stream) run
+ * concurrently and independently: each call has its own scratch and its own
+ * device error word.
  * Scratch: 9 padded fp32 fields and one fp64 field, ceil(nt / ckpt_every) x 3
  * checkpoint fields and
  * ckpt_every recomputation fields, from the library pool.  Synchronous. */

@@ -147,10 +147,6 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
         adjoint_prepared = 1;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    {
-        int pending = 0;
-        if ((rc = read_and_clear_dev_err(*ds, st, &pending))) return rc;
-    }
     const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
     const size_t fbytes = (size_t)L.elems * 4;
     const int nseg = (nt + C - 1) / C;
@@ -191,6 +187,7 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
     float *u0, *u1, *phi, *m, *w0, *w1, *mu0, *mu1, *gsum, *ck, *seg, *d_tr;
     double *gsum64, *d_J;
     long long *d_off;
+    int *d_err;  // this call's device error word: concurrent calls stay independent
     if ((rc = sc.get((void **)&u0, fbytes)) || (rc = sc.get((void **)&u1, fbytes)) ||
         (rc = sc.get((void **)&phi, fbytes)) || (rc = sc.get((void **)&m, fbytes)) ||
         (rc = sc.get((void **)&w0, fbytes)) || (rc = sc.get((void **)&w1, fbytes)) ||
@@ -200,8 +197,9 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
         (rc = sc.get((void **)&seg, fbytes * (size_t)C)) ||
         (rc = sc.get((void **)&d_tr, (size_t)nt * nrec * 4)) ||
         (rc = sc.get((void **)&gsum64, (size_t)L.elems * 8)) || (rc = sc.get((void **)&d_J, 8)) ||
-        (rc = sc.get((void **)&d_off, (size_t)nrec * 8)))
+        (rc = sc.get((void **)&d_off, (size_t)nrec * 8)) || (rc = sc.get((void **)&d_err, 16)))
         return rc;
+    CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), (size_t)nrec * 8, cudaMemcpyHostToDevice, st));
     for (float *f : {u0, u1, phi, m, w0, w1, mu0, mu1, gsum})
         CUDA_TRY(cudaMemsetAsync(f, 0, fbytes, st));
@@ -213,7 +211,7 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
     StepArgs base;
     fill_step_constants(g, L, base);
     base.phi = phi;
-    base.err = ds->err;
+    base.err = d_err;
     base.si = src_ijk[0];
     base.sj = src_ijk[1];
     base.sk = src_ijk[2];
@@ -243,7 +241,7 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
         if ((rc = launch_step<float>(a, fmaps[n & 1], grid, st))) return rc;
     }
     gather_kernel<<<(nrec + 255) / 256, 256, 0, st>>>(ubuf[(nt - 1) & 1], d_off, nrec,
-                                                      d_tr + (size_t)(nt - 1) * nrec, ds->err);
+                                                      d_tr + (size_t)(nt - 1) * nrec, d_err);
     CUDA_TRY(cudaGetLastError());
     double *d_part;
     if ((rc = sc.get((void **)&d_part, MISFIT_BLOCKS * 8))) return rc;
@@ -326,7 +324,8 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
     double J = 0.0;
     CUDA_TRY(cudaMemcpyAsync(&J, d_J, 8, cudaMemcpyDeviceToHost, st));
     int dev_err = 0;
-    if ((rc = read_and_clear_dev_err(*ds, st, &dev_err))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(&dev_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
     *misfit_out = J;
     if (dev_err & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a kernel wait timed out");
     return SGB_OK;

@@ -27,18 +27,54 @@ def my_shots(n_shots: int, rank: int, world: int) -> list:
     return list(range(rank, n_shots, world))
 
 
-def gradient_sum(shot_fn: Callable[[int], tuple], n_shots: int, like: torch.Tensor):
+def gradient_sum(shot_fn: Callable, n_shots: int, like: torch.Tensor, workers: int = 1,
+                 streams: Sequence | None = None):
     """Misfit and fp64 gradient summed over `n_shots` shots split across ranks.
 
-    shot_fn(i) returns (J_i, grad_i) for shot i (grad_i an fp64 tensor shaped
-    like `like`, on its device).  Returns (J, grad) on every rank."""
+    shot_fn(i, k) returns (J_i, grad_i) for shot i computed by worker k (grad_i
+    an fp64 tensor shaped like `like`, on its device, valid until that worker's
+    next call).  With workers > 1 each worker is a host thread (the library
+    releases the GIL while a shot runs), inside streams[k] when given, so the
+    shots' kernels overlap on the GPU.  Shot i goes to worker i mod workers and
+    every worker sums its shots in order, so the result does not depend on
+    timing.  Returns (J, grad) on every rank."""
+    import threading
+
     rank, world = _group_size()
-    total = torch.zeros_like(like, dtype=torch.float64)
-    J = 0.0
-    for i in my_shots(n_shots, rank, world):
-        Ji, gi = shot_fn(i)
-        J += float(Ji)
-        total += gi
+    mine = my_shots(n_shots, rank, world)
+    parts = [mine[k::workers] for k in range(workers)]
+    totals = [None] * workers
+    Js = [0.0] * workers
+    errors = []
+
+    def run(k):
+        try:
+            ctx = torch.cuda.stream(streams[k]) if streams is not None else _nullcontext()
+            with ctx:  # the sum lives on the worker's stream, like its shots
+                totals[k] = torch.zeros_like(like, dtype=torch.float64)
+                for i in parts[k]:
+                    Ji, gi = shot_fn(i, k)
+                    Js[k] += float(Ji)
+                    totals[k] += gi
+        except BaseException as e:  # re-raised in the caller's thread
+            errors.append(e)
+
+    if workers == 1:
+        run(0)
+    else:
+        threads = [threading.Thread(target=run, args=(k,)) for k in range(workers)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+    if errors:
+        raise errors[0]
+    if streams is not None:
+        torch.cuda.synchronize()
+    total = totals[0]
+    for t in totals[1:]:
+        total += t
+    J = sum(Js)
     if world > 1:
         import torch.distributed as dist
         dist.all_reduce(total, op=dist.ReduceOp.SUM)
@@ -46,6 +82,14 @@ def gradient_sum(shot_fn: Callable[[int], tuple], n_shots: int, like: torch.Tens
         dist.all_reduce(Jt, op=dist.ReduceOp.SUM)
         J = float(Jt.item())
     return J, total
+
+
+class _nullcontext:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
 
 
 def max_over_ranks(x: float, device=None) -> float:

@@ -34,7 +34,7 @@ def _case():
 def _shot_fn(case):
     go, v, wav, nt, shots, rec, obs = case
 
-    def fn(i):
+    def fn(i, k=0):
         J, g = oracle.adjoint_shot(go, v, wav, nt, shots[i], rec, obs[i].astype(np.float64))
         return J, torch.from_numpy(g)
     return fn
@@ -94,3 +94,16 @@ def test_gradient_sum_two_gloo_ranks_equals_one_process():
     assert np.abs(g1.numpy()).max() > 0
     # timing: the slowest rank's
     assert st[0][1] == st[1][1] == 2.5
+
+
+def test_gradient_sum_worker_threads_are_deterministic():
+    """Two worker threads (shot i on worker i mod 2, each summing in order) give
+    the same bits on every run, and the one-thread sum to fp64 reassociation."""
+    case = _case()
+    J1, g1 = replicas.gradient_sum(_shot_fn(case), N_SHOTS, torch.zeros(case[1].shape))
+    runs = [replicas.gradient_sum(_shot_fn(case), N_SHOTS, torch.zeros(case[1].shape), workers=2)
+            for _ in range(2)]
+    assert runs[0][0] == runs[1][0] and torch.equal(runs[0][1], runs[1][1])
+    np.testing.assert_allclose(runs[0][1].numpy(), g1.numpy(), rtol=1e-12,
+                               atol=1e-12 * np.abs(g1.numpy()).max())
+    assert abs(runs[0][0] - J1) <= 1e-12 * abs(J1)
