@@ -8,6 +8,8 @@ the hot path (interior update, fused PML, source injection, receiver
 sampling, the time loop) runs in each step.  Inputs are resident in HBM when
 the timed region starts; each of the four fields (u^n, u^{n-1}, m, phi) is
 ~571 MB, far above the 129 MB L2, so no L2 flush is needed between steps.
+The same JSON line carries the end-to-end figure (host buffers), the roofline
+of the step kernel, the 16-bit storage legs, a serving leg and a gradient leg.
 
 --impl reference times the fp64 CPU oracle on the host cores on bounded
 samples of the same workload.  Under torchrun every rank runs its own
@@ -273,8 +275,9 @@ def _gradient(a, seisgb, synth, peak):
     """Adjoint-gradient leg: 16 shots of the 256^3 / 2000-step workload, misfit
     against traces of the unperturbed model, gradients summed over the shots
     (fp64); shots/s, forward-equivalent Gpt/s and the whole computation's
-    algorithmic bytes per second against the HBM peak.  Under torchrun the shots
-    are split across ranks and one fp64 all-reduce sums the gradients."""
+    algorithmic bytes per second against the HBM peak.  Each rank keeps two shots
+    in flight on two streams (host threads); under torchrun the shots are split
+    across ranks and one fp64 all-reduce sums the gradients."""
     import torch
     from paper_2009_04619_gb300 import replicas
     rank, world, _ = _dist()
