@@ -57,10 +57,19 @@ __global__ void __launch_bounds__(Cfg::BLOCK, Cfg::MINB)
     multi_step_kernel(const ShotEntry *__restrict__ table, int nshots, int launch_i,
                       const int *__restrict__ replays, int steps_per_graph)
 {
+    // The CTA's shot: the number of shots whose first unit is <= blockIdx.x,
+    // minus one.  Each warp reads the start units in parallel (one lane per
+    // shot) instead of walking the table one dependent load at a time (no
+    // shared memory: the step's TMA destinations start at the dynamic base).
     const int b = blockIdx.x;
-    int s = 0;
-    while (s + 1 < nshots && b >= table[s + 1].unit_begin) ++s;
-    const ShotEntry &e = table[s];
+    const int lane = threadIdx.x & 31;
+    int count = 0;
+    for (int base = 0; base < nshots; base += 32) {
+        const int q = base + lane;
+        const bool le = q < nshots && table[q].unit_begin <= b;
+        count += __popc(__ballot_sync(0xffffffffu, le));
+    }
+    const ShotEntry &e = table[count - 1];
     const int n = e.n0 + *replays * steps_per_graph + launch_i;
     if (n > e.nt) return;  // finished: waits for retirement
     const CUtensorMap *mp = e.maps[n & 1];
