@@ -4,12 +4,14 @@ time per launch (CUDA events) -- a small driver for timing and for ncu captures.
     python -m paper_2009_04619_gb300.profile_step --n 256 --nb 32 --launches 20
     python -m paper_2009_04619_gb300.profile_step --adjoint --n 256 --nb 16 --nt 200
     python -m paper_2009_04619_gb300.profile_step --storage fp16 --n 512 --nb 32 --nt 40
+    python -m paper_2009_04619_gb300.profile_step --serve 16
 
 With --adjoint it runs one misfit-gradient shot instead (layered model with a
 Gaussian anomaly, observed traces from the model without it) and reports its
 time beside a forward shot of the same length.  With --storage fp16 or bf16 it
 runs a short run_shot with 16-bit wavefield storage (fp32 arithmetic) and
-reports the time per step.
+reports the time per step.  With --serve N it submits the first N requests of
+the seeded serving mix at once to a 16-slot server and reports shots/s.
 """
 from __future__ import annotations
 
@@ -81,6 +83,28 @@ def _storage(a):
                       "gpts": pts / ms / 1e6, "alg_gbs": alg / ms / 1e6}))
 
 
+def _serve(a):
+    import time
+    reqs = synth.serving_requests(256, seed=4)[:a.serve]
+    work = []
+    for r in reqs:
+        vmax = float(r["velocity"].max())
+        g0 = seisgb.make_grid(r["nx"], r["ny"], r["nz"], r["nb"], r["h"], r["h"], r["h"], 1.0, vmax)
+        dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, vmax)))
+        g = seisgb.make_grid(r["nx"], r["ny"], r["nz"], r["nb"], r["h"], r["h"], r["h"], dt, vmax)
+        work.append((g, r, synth.ricker(r["nt"], dt, r["fp"])))
+    with seisgb.Server(96 << 30, max_slots=16, steps_per_graph=16) as sv:
+        t0 = time.perf_counter()
+        tk = [sv.submit(g, r["velocity"], wav, r["nt"], r["src"], r["rec"]) for g, r, wav in work]
+        for t, (g, r, wav) in zip(tk, work):
+            sv.poll(t, r["nt"], r["rec"].shape[0], timeout_us=600_000_000)
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+    print(json.dumps({"requests": len(work), "shots_per_s": len(work) / wall, "wall_s": wall,
+                      "graph_replays": int(st.graph_replays), "wait_ms": st.wait_ms,
+                      "setup_ms": st.setup_ms}))
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--n", type=int, default=256, help="computed points per axis")
@@ -93,6 +117,8 @@ def main(argv=None):
     p.add_argument("--ckpt", type=int, default=100, help="checkpoint interval of the gradient shot")
     p.add_argument("--storage", choices=["fp16", "bf16"], default=None,
                    help="time a short run_shot with 16-bit wavefield storage")
+    p.add_argument("--serve", type=int, default=0,
+                   help="submit this many requests of the serving mix to a 16-slot server")
     a = p.parse_args(argv)
     if a.lib:
         seisgb.LIB_PATH = a.lib
@@ -103,6 +129,9 @@ def main(argv=None):
         return
     if a.storage:
         _storage(a)
+        return
+    if a.serve:
+        _serve(a)
         return
     n_in = a.n - 2 * a.nb  # nb = 0: no PML, every tile takes the interior path
     h, v = 10.0, 4500.0
