@@ -350,6 +350,38 @@ def _gradient(a, seisgb, synth, peak):
                         "central differences: tests"}
 
 
+def _small_case(a, seisgb, synth, dev, barrier):
+    """Gpt/s of the small forward-modelling case (64^3 inner + 16-point PML,
+    constant 2000 m/s, 100 steps) through run_shot, device-resident inputs,
+    CUDA events around `reps` back-to-back shots after a warm-up."""
+    import torch
+    w = synth.SMALL
+    vel = w.velocity()
+    g0 = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, 1.0, w.v_const)
+    dt = float(np.float32(w.cfl_fraction * seisgb.cfl_dt(g0, w.v_const)))
+    g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, w.v_const)
+    rec = w.receivers()
+    d_v = torch.from_numpy(vel).to(dev)
+    d_w = torch.from_numpy(synth.ricker(w.nt, dt, w.fp)).to(dev)
+    tr = torch.zeros((w.nt, rec.shape[0]), dtype=torch.float32, device=dev)
+    for _ in range(max(3, a.warmup)):
+        seisgb.run_shot(g, d_v, d_w, w.nt, w.source(), rec, tr)
+    barrier()
+    reps = 20
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        seisgb.run_shot(g, d_v, d_w, w.nt, w.source(), rec, tr)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": w.name, "grid": list(w.shape), "nt": w.nt, "value": w.points * w.nt / ms / 1e6,
+            "unit": UNIT, "ms_per_shot": ms,
+            "note": "fields fit in L2 (4 x 4.5 MB): no roofline claim; includes run_shot's per-call "
+                    "set-up (allocation, m, velocity range check, graph capture)"}
+
+
 def run_reference(a):
     rank, world, _ = _dist()
     if rank != 0:
@@ -508,6 +540,11 @@ def main():
             "frac": alg16 / (pms / w.nt / 1e3) / 1e9 / peak,
             "error": "relative L2 vs the fp64 oracle: see the 256^3 x 1000-step precision test"}
 
+    # the small forward-modelling case (64^3 inner + 16-point PML, 100 steps):
+    # whole shots through run_shot, device-resident inputs (its four fields fit
+    # in L2, so no roofline claim is made for it)
+    small = _small_case(a, seisgb, synth, dev, barrier)
+
     serving = _serving(a, seisgb, synth, value) if a.serve_requests > 0 else None
     gradient = _gradient(a, seisgb, synth, peak) if a.grad_shots > 0 else None
 
@@ -529,6 +566,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "precision": precision,
+        "small_case": small,
         "serving": serving,
         "gradient": gradient,
     }
@@ -538,10 +576,24 @@ def main():
         cores = os.cpu_count() or 1
         S = a.oracle_steps
         dt_s, ts, t0 = _time_oracle(w, vel, wav, src, rec, S, cores)
+        S1 = max(1, S // 20)
+        dt_1, _, _ = _time_oracle(w, vel, wav, src, rec, S1, 1)
+        ws = synth.SMALL
+        vs = ws.velocity()
+        dts = float(np.float32(ws.cfl_fraction * oracle.cfl_dt(ws.v_const, ws.h, ws.h, ws.h)))
+        wavs = synth.ricker(ws.nt, dts, ws.fp)
+        small_all, _, _ = _time_oracle(ws, vs, wavs, ws.source(), ws.receivers(), ws.nt, cores)
+        small_1, _, _ = _time_oracle(ws, vs, wavs, ws.source(), ws.receivers(), ws.nt, 1)
         out["cpu_baseline"] = {
             "value": w.points * S / dt_s / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"{S} of {w.nt} time steps of the {w.name} workload "
-                       f"({ts:.1f} s call minus {t0:.1f} s oracle set-up), fp64, {cores} threads")}
+                       f"({ts:.1f} s call minus {t0:.1f} s oracle set-up), fp64, {cores} threads"),
+            "single_thread": {"value": w.points * S1 / dt_1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"{S1} time steps of the same workload, one thread"},
+            "small_case": {"workload": ws.name, "unit": UNIT,
+                           "value": ws.points * ws.nt / small_all / 1e9, "cores": cores,
+                           "value_single_thread": ws.points * ws.nt / small_1 / 1e9,
+                           "sample": "the whole 100-step shot, all cores and one thread"}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -103,7 +103,9 @@ int sgb_cfl_dt(const sgb_grid *g, float vmax, float *dt_max);
  * u fields are fp32 (storage SGB_FP32).  step selects src->wavelet[step].
  * src and rec may be NULL.  All device pointers must be 16-byte aligned.
  * Asynchronous on stream.  UNSTABLE_DT when g->dt exceeds the CFL limit for
- * g->vmax. */
+ * g->vmax.  A bounded kernel wait that gave up or a non-finite receiver sample
+ * sets a bit of this device's stencil_step error word, which
+ * sgb_device_status reads and clears. */
 int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next, const float *m,
                  float *phi, int32_t step, const sgb_source *src, const sgb_receivers *rec,
                  void *stream);
@@ -116,10 +118,14 @@ int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next, con
  *   rec_ijk   host int32[nrec*3]
  *   traces    nt*nrec fp32, host or device; traces[n*nrec + r] = u^{n+1}(rec_r)
  *   final_u   Nz*Ny*Nx fp32 compact u^{nt}, host or device, or NULL
- * Scratch (two wavefields, phi, m) comes from a library-owned stream-ordered
- * pool and is released before returning.  Enqueued on stream, then the call
- * waits for the stream.  UNSTABLE_DT if dt exceeds the CFL limit of the
- * model's actual maximum velocity; NONFINITE if a receiver saw a NaN/Inf. */
+ * Scratch (two wavefields, phi, m, a device error word of this call's own)
+ * comes from a library-owned stream-ordered pool and is released before
+ * returning.  Enqueued on stream, then the call waits for the stream.
+ * INVALID_ARG if traces or final_u overlaps velocity, wavelet or each other;
+ * UNSTABLE_DT if dt exceeds the CFL limit of the model's actual maximum
+ * velocity; NONFINITE if a receiver saw a NaN/Inf (traces are still written);
+ * TIMEOUT if a kernel's bounded wait gave up.  Calls on different streams are
+ * independent. */
 int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
              const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
              float *final_u, void *stream);
@@ -166,8 +172,10 @@ int adjoint_shot(const sgb_grid *g, const float *velocity, const float *wavelet,
  *  - the first call on a device resolves the array's device address (set-up);
  *    make that first call before any stream capture;
  *  - all calls share the array and it keeps the previous call's contents (each
- *    call clears what must start at zero); calls whose GPU work overlaps, on
- *    any streams, race on it and give wrong results;
+ *    call clears what must start at zero, including the error word it keeps
+ *    there); calls whose GPU work overlaps, on any streams, race on it and give
+ *    wrong results or statuses;
+ *  - like run_shot, outputs that overlap an input or each other are rejected;
  *  - the time loop is launched directly, one kernel per step (no CUDA graph). */
 int run_shot_noalloc(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
                      const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
@@ -203,10 +211,15 @@ typedef struct {
 
 typedef struct {
     uint64_t ticket;
-    int32_t status;             /* SGB_OK or the error that ended the shot */
+    int32_t status;             /* SGB_OK or the error that ended the shot:
+                                   TIMEOUT (a kernel wait gave up), NONFINITE (a
+                                   receiver sampled NaN/Inf), OUT_OF_MEMORY,
+                                   CUDA_ERROR; each shot has its own device
+                                   error word */
     int32_t nt, nrec;
     float *traces;              /* caller buffer of nt*nrec floats (or NULL);
-                                   filled when serve_poll returns SGB_OK */
+                                   filled when serve_poll returns SGB_OK and
+                                   status is SGB_OK or SGB_ERR_NONFINITE */
     double queue_ms;            /* submit -> admission */
     double latency_ms;          /* submit -> traces on the host */
 } sgb_shot_result;
@@ -251,20 +264,21 @@ int serve_destroy(sgb_server *s);
 int sgb_pack(const sgb_grid *g, const float *compact, float *padded, void *stream);
 int sgb_unpack(const sgb_grid *g, const float *padded, float *compact, void *stream);
 
-/* Reads (and clears) the device-side error word that kernels set when a
- * bounded wait gave up or an input was out of range; synchronises stream.
- * Returns SGB_OK, SGB_ERR_TIMEOUT or SGB_ERR_CUDA. */
+/* Reads and clears, in one atomic step on the device, the current device's
+ * stencil_step error word (set when a bounded kernel wait gave up or a
+ * receiver sampled NaN/Inf); synchronises stream.  Returns SGB_OK,
+ * SGB_ERR_TIMEOUT, SGB_ERR_NONFINITE or SGB_ERR_CUDA.  Other entry points
+ * report through error words of their own and are not seen here. */
 int sgb_device_status(void *stream);
 
 /* Self-test of the failure detection the step kernels use (no counterpart in
  * the paper): launches one kernel whose bounded wait on an mbarrier that
  * nothing completes -- the wait of a step whose TMA copies never land -- gives
- * up after limit_us microseconds (1..2,000,000) and sets the timeout bit of the
- * device error word, which the host then reads and clears as
- * sgb_device_status does.  *status_out receives that status (SGB_ERR_TIMEOUT
- * when detection works); the return value is SGB_OK unless the arguments are
- * invalid or the launch failed.  No GPU fault is involved and the context
- * stays usable.  Synchronises stream. */
+ * up after limit_us microseconds (1..2,000,000) and sets the timeout bit of an
+ * error word of the call's own, which the host then reads.  *status_out
+ * receives that status (SGB_ERR_TIMEOUT when detection works); the return
+ * value is SGB_OK unless the arguments are invalid or the launch failed.  No
+ * GPU fault is involved and the context stays usable.  Synchronises stream. */
 int sgb_selftest_wait_timeout(int32_t limit_us, int32_t *status_out, void *stream);
 
 /* Number of this library's kernels launched by the calling thread since the

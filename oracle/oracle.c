@@ -407,18 +407,26 @@ int ora_adjoint_shot(const ora_grid *g, const float *velocity, const float *wave
     long sx = Nx + 2 * R, sxy = sx * (Ny + 2 * R);
     const long st3[3] = {1, sx, sxy};
     const double hh[3] = {g->dx, g->dy, g->dz};
-    double *m = calloc(n, sizeof(double)), *eta = calloc(n, sizeof(double));
-    double *ua = calloc(n, sizeof(double)), *ub = calloc(n, sizeof(double)), *uc = calloc(n, sizeof(double));
-    double *pa = calloc(n, sizeof(double)), *pb = calloc(n, sizeof(double));
-    double *lap = calloc(n, sizeof(double));
-    double *gacc = calloc(n * (size_t)nt, sizeof(double));
-    double *traces = calloc((size_t)nt * (nrec > 0 ? nrec : 1), sizeof(double));
-    double *w1 = calloc(n, sizeof(double)), *w2 = calloc(n, sizeof(double)), *wk = calloc(n, sizeof(double));
-    double *nu = calloc(n, sizeof(double)), *nun = calloc(n, sizeof(double)), *psi = calloc(n, sizeof(double));
-    double *gm = calloc(n, sizeof(double)), *wl = calloc(n, sizeof(double));
-    if (!m || !eta || !ua || !ub || !uc || !pa || !pb || !lap || !gacc || !traces || !w1 || !w2 ||
-        !wk || !nu || !nun || !psi || !gm || !wl)
+    /* every work array in one table, so that a failed allocation frees the rest */
+    enum { A_M, A_ETA, A_UA, A_UB, A_UC, A_PA, A_PB, A_LAP, A_GACC, A_TR, A_W1, A_W2, A_WK,
+           A_NU, A_NUN, A_PSI, A_GM, A_WL, A_COUNT };
+    double *arr[A_COUNT];
+    int ok = 1;
+    for (int q = 0; q < A_COUNT; ++q) {
+        size_t len = q == A_GACC ? n * (size_t)nt
+                   : q == A_TR   ? (size_t)nt * (nrec > 0 ? nrec : 1)
+                                 : n;
+        arr[q] = calloc(len, sizeof(double));
+        ok = ok && arr[q] != NULL;
+    }
+    if (!ok) {
+        for (int q = 0; q < A_COUNT; ++q) free(arr[q]);
         return -1;
+    }
+    double *m = arr[A_M], *eta = arr[A_ETA], *ua = arr[A_UA], *ub = arr[A_UB], *uc = arr[A_UC];
+    double *pa = arr[A_PA], *pb = arr[A_PB], *lap = arr[A_LAP], *gacc = arr[A_GACC];
+    double *traces = arr[A_TR], *w1 = arr[A_W1], *w2 = arr[A_W2], *wk = arr[A_WK];
+    double *nu = arr[A_NU], *nun = arr[A_NUN], *psi = arr[A_PSI], *gm = arr[A_GM], *wl = arr[A_WL];
     double dt = g->dt;
     for (int k = 0; k < Nz; ++k)
         for (int j = 0; j < Ny; ++j)
@@ -527,7 +535,6 @@ int ora_adjoint_shot(const ora_grid *g, const float *velocity, const float *wave
                 double v = (double)velocity[((size_t)k * Ny + j) * Nx + i];
                 grad_v[((size_t)k * Ny + j) * Nx + i] = gm[p] * 2.0 * v * dt * dt;
             }
-    free(m); free(eta); free(ua); free(ub); free(uc); free(pa); free(pb); free(lap); free(gacc);
-    free(traces); free(w1); free(w2); free(wk); free(nu); free(nun); free(psi); free(gm); free(wl);
+    for (int q = 0; q < A_COUNT; ++q) free(arr[q]);
     return 0;
 }

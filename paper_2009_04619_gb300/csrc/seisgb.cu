@@ -57,7 +57,9 @@ extern "C" int64_t sgb_launch_count(int reset)
     return v;
 }
 
-// Device error word set by kernels (bounded-wait timeouts, non-finite samples).
+// Device error word of stencil_step (bounded-wait timeouts, non-finite
+// samples), read and cleared by sgb_device_status.  run_shot, run_shot_noalloc,
+// adjoint_shot, the self-test and every served shot have words of their own.
 static __device__ int g_dev_err;
 
 // ---------------------------------------------------------------------------
@@ -354,13 +356,62 @@ struct Scratch {
     }
 };
 
-int read_and_clear_dev_err(const DevState &ds, cudaStream_t st, int *val)
+// out = err, err = 0 in one atomic step: a bit set by a kernel on another
+// stream between a read and a separate clear would otherwise be lost.
+__global__ void take_err_kernel(int *err, int *out)
 {
-    int zero = 0;
-    CUDA_TRY(cudaMemcpyAsync(val, ds.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = atomicExch(err, 0);
+}
+
+// Read and clear the error word `err` (stream-ordered, then waits for st).
+int read_and_clear_dev_err(int *err, const DevState &ds, cudaStream_t st, int *val)
+{
+    Scratch sc{st, ds.pool, {}};
+    int *d_out = nullptr;
+    int rc = sc.get((void **)&d_out, sizeof(int));
+    if (rc) return rc;
+    take_err_kernel<<<1, 32, 0, st>>>(err, d_out);
+    CUDA_TRY(cudaGetLastError());
+    ++t_launches;
+    CUDA_TRY(cudaMemcpyAsync(val, d_out, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    CUDA_TRY(cudaMemcpyAsync(ds.err, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    return SGB_OK;
+}
+
+// Map the bits of an error word to the status a call returns.
+int dev_err_status(int v)
+{
+    if (v & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a kernel wait timed out");
+    if (v & DEV_ERR_NONFINITE) return fail(SGB_ERR_NONFINITE, "a receiver sampled NaN/Inf");
+    if (v) return fail(SGB_ERR_CUDA, "device error word %d", v);
+    return SGB_OK;
+}
+
+// A byte range of a caller buffer (host or device: one address space).
+struct Span {
+    const void *p;
+    size_t bytes;
+    const char *name;
+};
+
+bool spans_overlap(const Span &a, const Span &b)
+{
+    if (!a.p || !b.p || !a.bytes || !b.bytes) return false;
+    const uintptr_t a0 = (uintptr_t)a.p, b0 = (uintptr_t)b.p;
+    return a0 < b0 + b.bytes && b0 < a0 + a.bytes;
+}
+
+// Outputs may overlap neither an input nor each other.
+int check_no_overlap(const Span *outs, int nout, const Span *ins, int nin)
+{
+    for (int o = 0; o < nout; ++o) {
+        for (int i = 0; i < nin; ++i)
+            if (spans_overlap(outs[o], ins[i]))
+                return fail(SGB_ERR_INVALID_ARG, "%s overlaps %s", outs[o].name, ins[i].name);
+        for (int q = o + 1; q < nout; ++q)
+            if (spans_overlap(outs[o], outs[q]))
+                return fail(SGB_ERR_INVALID_ARG, "%s overlaps %s", outs[o].name, outs[q].name);
+    }
     return SGB_OK;
 }
 
@@ -447,12 +498,16 @@ extern "C" int sgb_selftest_wait_timeout(int32_t limit_us, int32_t *status_out, 
     int rc = device_state(&ds);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    int v = 0;
-    if ((rc = read_and_clear_dev_err(*ds, st, &v))) return rc;  // earlier errors are not ours
-    wait_timeout_probe_kernel<<<1, 32, 0, st>>>(ds->err, (unsigned long long)limit_us * 1000ull);
+    Scratch sc{st, ds->pool, {}};
+    int *d_err = nullptr;  // this call's own error word
+    if ((rc = sc.get((void **)&d_err, sizeof(int)))) return rc;
+    CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    wait_timeout_probe_kernel<<<1, 32, 0, st>>>(d_err, (unsigned long long)limit_us * 1000ull);
     CUDA_TRY(cudaGetLastError());
     ++t_launches;
-    if ((rc = read_and_clear_dev_err(*ds, st, &v))) return rc;
+    int v = 0;
+    CUDA_TRY(cudaMemcpyAsync(&v, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
     *status_out = (v & DEV_ERR_TIMEOUT) ? SGB_ERR_TIMEOUT : v ? SGB_ERR_CUDA : SGB_OK;
     return SGB_OK;
 }
@@ -463,11 +518,8 @@ extern "C" int sgb_device_status(void *stream)
     int rc = device_state(&ds);
     if (rc) return rc;
     int v = 0;
-    if ((rc = read_and_clear_dev_err(*ds, (cudaStream_t)stream, &v))) return rc;
-    if (v & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a kernel wait timed out");
-    if (v & DEV_ERR_NONFINITE) return fail(SGB_ERR_NONFINITE, "non-finite receiver sample");
-    if (v) return fail(SGB_ERR_CUDA, "device error word %d", v);
-    return SGB_OK;
+    if ((rc = read_and_clear_dev_err(ds->err, *ds, (cudaStream_t)stream, &v))) return rc;
+    return dev_err_status(v);
 }
 
 extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
@@ -552,7 +604,7 @@ template <class T>
 int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
                Scratch &sc, const float *d_vel, const float *d_wav, int nt,
                const int32_t *src_ijk, int nrec, const long long *d_off, float *d_tr,
-               float *final_u)
+               float *final_u, int *d_err)
 {
     int rc;
     const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
@@ -585,7 +637,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     StepArgs base;
     fill_step_constants(g, L, base);
     base.phi = phi;
-    base.err = ds->err;
+    base.err = d_err;
     base.scale = ss;
     if (src_ijk) {
         base.si = src_ijk[0];
@@ -657,7 +709,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     if (nrec > 0 && nt > 0) {
         gather_t_kernel<T><<<(nrec + 255) / 256, 256, 0, st>>>(
             static_cast<const T *>(u_final_dev), d_off, nrec, s_final,
-            d_tr + (size_t)(nt - 1) * nrec, ds->err);
+            d_tr + (size_t)(nt - 1) * nrec, d_err);
         CUDA_TRY(cudaGetLastError());
         ++t_launches;
     }
@@ -700,16 +752,22 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
                         i, j, k);
         off[r] = L.origin + (long long)k * L.stride_z + (long long)j * L.sx + i;
     }
+    const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
+    {
+        const Span ins[] = {{velocity, (size_t)ncomp * 4, "velocity"},
+                            {src_ijk ? wavelet : nullptr, (size_t)nt * 4, "wavelet"}};
+        const Span outs[] = {{nrec > 0 ? traces : nullptr, (size_t)nt * nrec * 4, "traces"},
+                             {final_u, (size_t)ncomp * 4, "final_u"}};
+        if ((rc = check_no_overlap(outs, 2, ins, 2))) return rc;
+    }
     DevState *ds;
     if ((rc = device_state(&ds))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
-    {
-        int pending = 0;
-        if ((rc = read_and_clear_dev_err(*ds, st, &pending))) return rc;
-    }
 
     Scratch sc{st, ds->pool, {}};
+    int *d_err = nullptr;  // this call's own device error word
+    if ((rc = sc.get((void **)&d_err, sizeof(int)))) return rc;
+    CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     const float *d_vel = velocity;
     if (!is_device_ptr(velocity)) {
         float *t;
@@ -754,23 +812,22 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     }
     switch (g->storage) {
     case SGB_FP16_SCALED:
-        rc = run_shot_t<__half>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u);
+        rc = run_shot_t<__half>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u, d_err);
         break;
     case SGB_BF16:
         rc = run_shot_t<__nv_bfloat16>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
-                                       final_u);
+                                       final_u, d_err);
         break;
     default:
-        rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u);
+        rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u, d_err);
     }
     if (rc) return rc;
     if (host_traces && nt > 0)
         CUDA_TRY(cudaMemcpyAsync(traces, d_tr, (size_t)nt * nrec * 4, cudaMemcpyDeviceToHost, st));
     int dev_err = 0;
-    if ((rc = read_and_clear_dev_err(*ds, st, &dev_err))) return rc;
-    if (dev_err & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a step kernel wait timed out");
-    if (dev_err & DEV_ERR_NONFINITE) return fail(SGB_ERR_NONFINITE, "a receiver sampled NaN/Inf");
-    return SGB_OK;
+    CUDA_TRY(cudaMemcpyAsync(&dev_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return dev_err_status(dev_err);
 }
 
 // ---------------------------------------------------------------------------
@@ -794,13 +851,12 @@ namespace {
 struct NoAllocState {
     bool ready = false;
     unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch
-    int *err = nullptr;                // device address of g_dev_err
     int sms = 0, occ = 0;
 };
 NoAllocState g_noalloc[64];
 
-// Once per device, with that device current: resolve the device addresses of
-// the scratch array and the error word, and the step kernel's launch limits.
+// Once per device, with that device current: resolve the device address of
+// the scratch array and the step kernel's launch limits.
 int noalloc_setup(NoAllocState **out)
 {
     int dev = 0;
@@ -810,7 +866,6 @@ int noalloc_setup(NoAllocState **out)
     NoAllocState &s = g_noalloc[dev];
     if (!s.ready) {
         CUDA_TRY(cudaGetSymbolAddress((void **)&s.scratch, g_noalloc_scratch));
-        CUDA_TRY(cudaGetSymbolAddress((void **)&s.err, g_dev_err));
         CUDA_TRY(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev));
         int rc0;
         if ((rc0 = prepare_step_kernel<float>(&s.occ))) return rc0;
@@ -862,12 +917,20 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
     for (int r = 0; r < nrec; ++r)
         if (!in_inner(g, rec_ijk[3 * r], rec_ijk[3 * r + 1], rec_ijk[3 * r + 2]))
             return fail(SGB_ERR_INVALID_ARG, "receiver %d outside the inner region", r);
+    const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
+    {
+        const Span ins[] = {{velocity, (size_t)ncomp * 4, "velocity"},
+                            {src_ijk ? wavelet : nullptr, (size_t)nt * 4, "wavelet"}};
+        const Span outs[] = {{nrec > 0 ? traces : nullptr, (size_t)nt * nrec * 4, "traces"},
+                             {final_u, (size_t)ncomp * 4, "final_u"}};
+        if ((rc = check_no_overlap(outs, 2, ins, 2))) return rc;
+    }
     // scratch layout inside the fixed array
     const size_t fbytes = align256((size_t)L.elems * 4);
     const size_t off_u0 = 0, off_u1 = fbytes, off_phi = 2 * fbytes, off_m = 3 * fbytes;
     const size_t off_ijk = 4 * fbytes;
     const size_t off_rec = off_ijk + align256((size_t)nrec * 12);
-    const size_t off_range = off_rec + align256((size_t)nrec * 8);
+    const size_t off_range = off_rec + align256((size_t)nrec * 8);  // range[4], then error word
     const size_t need = off_range + 256;
     if (need > SGB_NOALLOC_SCRATCH_BYTES)
         return fail(SGB_ERR_INVALID_ARG,
@@ -888,16 +951,12 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
     int32_t *d_ijk = (int32_t *)(base + off_ijk);
     long long *d_off = (long long *)(base + off_rec);
     int *d_range = (int *)(base + off_range);
-    const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
+    int *d_err = d_range + 4;  // this entry point's own error word
     const int ewg = (int)std::min<long long>((ncomp + 255) / 256, (long long)ns->sms * 8);
 
     // the array keeps the previous call's contents: clear what must start at zero
-    int zero = 0, dev_err = 0;
-    CUDA_TRY(cudaMemcpyAsync(&dev_err, ns->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    CUDA_TRY(cudaMemcpyAsync(ns->err, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemsetAsync(base, 0, off_ijk, st));  // u0, u1, phi, m
-    int init[4] = {0, 0x7f7fffff, 0, 0};
+    int init[8] = {0, 0x7f7fffff, 0, 0, 0, 0, 0, 0};  // velocity range; error word = 0
     CUDA_TRY(cudaMemcpyAsync(d_range, init, sizeof init, cudaMemcpyHostToDevice, st));
     vel_range_kernel<<<ewg, 256, 0, st>>>(velocity, ncomp, d_range);
     CUDA_TRY(cudaGetLastError());
@@ -926,7 +985,7 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
     StepArgs base_args;
     fill_step_constants(g, L, base_args);
     base_args.phi = phi;
-    base_args.err = ns->err;
+    base_args.err = d_err;
     if (src_ijk) {
         base_args.si = src_ijk[0];
         base_args.sj = src_ijk[1];
@@ -952,7 +1011,7 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
     float *u_last = nt > 0 ? buf[(nt - 1) & 1] : buf[1];
     if (nrec > 0 && nt > 0) {
         gather_kernel<<<(nrec + 255) / 256, 256, 0, st>>>(u_last, d_off, nrec,
-                                                          traces + (size_t)(nt - 1) * nrec, ns->err);
+                                                          traces + (size_t)(nt - 1) * nrec, d_err);
         CUDA_TRY(cudaGetLastError());
         ++t_launches;
     }
@@ -961,15 +1020,10 @@ extern "C" int run_shot_noalloc(const sgb_grid *g, const float *velocity, const 
         CUDA_TRY(cudaGetLastError());
         ++t_launches;
     }
-    CUDA_TRY(cudaMemcpyAsync(&dev_err, ns->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int dev_err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&dev_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    if (dev_err) {
-        CUDA_TRY(cudaMemcpyAsync(ns->err, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-    }
-    if (dev_err & DEV_ERR_TIMEOUT) return fail(SGB_ERR_TIMEOUT, "a step kernel wait timed out");
-    if (dev_err & DEV_ERR_NONFINITE) return fail(SGB_ERR_NONFINITE, "a receiver sampled NaN/Inf");
-    return SGB_OK;
+    return dev_err_status(dev_err);
 }
 
 #include "serve_impl.cuh"

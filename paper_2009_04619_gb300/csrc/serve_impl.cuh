@@ -101,6 +101,7 @@ struct Shot {
     float *u0 = nullptr, *u1 = nullptr, *phi = nullptr, *m = nullptr, *d_vel = nullptr,
           *d_wav = nullptr, *d_tr = nullptr;
     long long *d_off = nullptr;
+    int *d_err = nullptr;  // this shot's device error word (timeouts, non-finite samples)
     ShotEntry entry;
     int n0 = 0;  // next step to run
     Clock::time_point t_submit, t_admit, t_done;
@@ -154,6 +155,10 @@ void free_shot_device(sgb_server *sv, Shot *sh)
         cudaFreeAsync(sh->d_off, sv->stream);
         sh->d_off = nullptr;
     }
+    if (sh->d_err) {
+        cudaFreeAsync(sh->d_err, sv->stream);
+        sh->d_err = nullptr;
+    }
 }
 
 // Fields, m, receiver table and step arguments of a newly admitted shot
@@ -178,7 +183,8 @@ int setup_shot(sgb_server *sv, Shot *sh)
         (rc = get((void **)&sh->d_vel, (size_t)ncomp * 4)) ||
         (rc = get((void **)&sh->d_wav, (size_t)sh->nt * 4)) ||
         (rc = get((void **)&sh->d_tr, (size_t)sh->nt * sh->nrec * 4)) ||
-        (rc = get((void **)&sh->d_off, (size_t)sh->nrec * 8)))
+        (rc = get((void **)&sh->d_off, (size_t)sh->nrec * 8)) ||
+        (rc = get((void **)&sh->d_err, sizeof(int))))
         return rc;
     std::vector<long long> off(sh->nrec);
     for (int r = 0; r < sh->nrec; ++r)
@@ -187,6 +193,7 @@ int setup_shot(sgb_server *sv, Shot *sh)
     CUDA_TRY(cudaMemcpyAsync(sh->d_vel, sh->vel.data(), (size_t)ncomp * 4, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(sh->d_wav, sh->wav.data(), (size_t)sh->nt * 4, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(sh->d_off, off.data(), (size_t)sh->nrec * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(sh->d_err, 0, sizeof(int), st));
     CUDA_TRY(cudaMemsetAsync(sh->u0, 0, fbytes, st));
     CUDA_TRY(cudaMemsetAsync(sh->u1, 0, fbytes, st));
     CUDA_TRY(cudaMemsetAsync(sh->phi, 0, fbytes, st));
@@ -204,7 +211,7 @@ int setup_shot(sgb_server *sv, Shot *sh)
     StepArgs a;
     fill_step_constants(&sh->g, L, a);
     a.phi = sh->phi;
-    a.err = sv->ds->err;
+    a.err = sh->d_err;
     a.si = sh->src[0];
     a.sj = sh->src[1];
     a.sk = sh->src[2];
@@ -239,18 +246,30 @@ int setup_shot(sgb_server *sv, Shot *sh)
     return SGB_OK;
 }
 
-// Retire a finished shot: traces to the host, device memory back to the pool.
+// Retire a finished shot: its error word decides its status (a kernel wait
+// that timed out, a receiver that sampled NaN/Inf); traces to the host, device
+// memory back to the pool.
 int retire_shot(sgb_server *sv, Shot *sh)
 {
     sh->traces.resize((size_t)sh->nt * sh->nrec);
     int rc = SGB_OK;
     if (sh->status == SGB_OK) {
-        cudaError_t e = cudaMemcpyAsync(sh->traces.data(), sh->d_tr, sh->traces.size() * 4,
-                                        cudaMemcpyDeviceToHost, sv->stream);
+        int v = 0;
+        cudaError_t e = cudaMemcpyAsync(&v, sh->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                        sv->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sh->traces.data(), sh->d_tr, sh->traces.size() * 4,
+                                cudaMemcpyDeviceToHost, sv->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
         if (e != cudaSuccess) {
             sh->status = SGB_ERR_CUDA;
             rc = fail(SGB_ERR_CUDA, "serve: trace copy failed: %s", cudaGetErrorString(e));
+        } else if (v & DEV_ERR_TIMEOUT) {
+            sh->status = SGB_ERR_TIMEOUT;
+        } else if (v & DEV_ERR_NONFINITE) {
+            sh->status = SGB_ERR_NONFINITE;
+        } else if (v) {
+            sh->status = SGB_ERR_CUDA;
         }
     }
     free_shot_device(sv, sh);
@@ -422,14 +441,7 @@ void scheduler(sgb_server *sv)
                 else keep.push_back(sh);
             }
         }
-        int dev_err = 0;
-        if (!finished.empty()) {
-            read_and_clear_dev_err(*sv->ds, sv->stream, &dev_err);
-            for (Shot *sh : finished) {
-                if (sh->status == SGB_OK && (dev_err & DEV_ERR_TIMEOUT)) sh->status = SGB_ERR_TIMEOUT;
-                retire_shot(sv, sh);
-            }
-        }
+        for (Shot *sh : finished) retire_shot(sv, sh);
         for (Shot *sh : joined) keep.push_back(sh);
         if (!finished.empty() || !joined.empty()) sv->composition_changed = true;
         t_retire = ms_between(tp, Clock::now());
@@ -592,7 +604,7 @@ extern "C" int serve_poll(sgb_server *sv, uint64_t ticket, sgb_shot_result *out,
     out->nrec = sh->nrec;
     out->queue_ms = ms_between(sh->t_submit, sh->t_admit);
     out->latency_ms = ms_between(sh->t_submit, sh->t_done);
-    if (out->traces && sh->status == SGB_OK)
+    if (out->traces && (sh->status == SGB_OK || sh->status == SGB_ERR_NONFINITE))
         memcpy(out->traces, sh->traces.data(), sh->traces.size() * 4);
     sv->done.erase(ticket);
     sv->known.erase(ticket);

@@ -1,10 +1,10 @@
 """Launch the fused step kernel back to back on a synthetic grid and report its
 time per launch (CUDA events) -- a small driver for timing and for ncu captures.
 
-    python -m paper_2009_04619_gb300.profile_step --n 256 --nb 32 --launches 20
-    python -m paper_2009_04619_gb300.profile_step --adjoint --n 256 --nb 16 --nt 200
-    python -m paper_2009_04619_gb300.profile_step --storage fp16 --n 512 --nb 32 --nt 40
-    python -m paper_2009_04619_gb300.profile_step --serve 16
+    python profile_step.py --n 256 --nb 32 --launches 20
+    python profile_step.py --adjoint --n 256 --nb 16 --nt 200
+    python profile_step.py --storage fp16 --n 512 --nb 32 --nt 40
+    python profile_step.py --serve 16
 
 With --adjoint it runs one misfit-gradient shot instead (layered model with a
 Gaussian anomaly, observed traces from the model without it) and reports its
@@ -17,11 +17,17 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
+import sys
 
 import numpy as np
 import torch
 
-from . import build, seisgb, synth
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2009_04619_gb300 import build, seisgb, synth  # noqa: E402
 
 
 def _adjoint(a):

@@ -129,6 +129,38 @@ def test_run_shot_argument_checks_without_gpu(lib):
     assert rc == seisgb.ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("entry", ["run_shot", "run_shot_noalloc"])
+def test_outputs_overlapping_inputs_rejected_without_gpu(lib, entry):
+    """traces and final_u may overlap neither velocity, wavelet nor each other
+    (checked before any GPU work, for both shot entry points)."""
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
+    f = getattr(seisgb.lib(), entry)
+    N = int(np.prod(g.shape))
+    nt = 10
+    big = np.zeros(4 * N, np.float32)
+    v = big[:N]
+    v[:] = 2000.0
+    w = np.zeros(nt, np.float32)
+    src = np.array([5, 5, 5], np.int32)
+    rec = np.array([[5, 5, 2]], np.int32)
+    tr = np.zeros(nt, np.float32)
+    base = big.ctypes.data
+
+    def call(tr_ptr, u_ptr, w_ptr=w.ctypes.data):
+        rc = f(ctypes.byref(g), base, w_ptr, nt, src.ctypes.data, rec.ctypes.data, 1, tr_ptr, u_ptr,
+               None)
+        return rc, seisgb.last_error()
+
+    rc, msg = call(tr.ctypes.data, base + 4 * (N // 2))  # final_u inside velocity
+    assert rc == seisgb.ERR_INVALID_ARG and "final_u overlaps velocity" in msg
+    rc, msg = call(base + 4 * (N - 1), None)  # traces start on velocity's last element
+    assert rc == seisgb.ERR_INVALID_ARG and "traces overlaps velocity" in msg
+    rc, msg = call(base + 4 * (2 * N), base + 4 * (2 * N + 5))  # traces inside final_u
+    assert rc == seisgb.ERR_INVALID_ARG and "overlaps" in msg
+    rc, msg = call(base + 4 * N, None, w_ptr=base + 4 * N + 8)  # traces over the wavelet
+    assert rc == seisgb.ERR_INVALID_ARG and "traces overlaps wavelet" in msg
+
+
 def test_serve_footprint_arithmetic(lib):
     """Four padded fp32 fields + velocity upload + wavelet + receiver table + traces."""
     g = seisgb.make_grid(20, 24, 16, 6, 10, 10, 10, 1e-3, 3000)

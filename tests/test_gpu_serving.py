@@ -1,6 +1,8 @@
 """Continuous-batching shot server: each result equals run_shot's for the same
-request whether it ran alone or in a mix of different grid sizes; admission
-respects the HBM budget; over-budget requests are rejected; polls time out."""
+request (bit for bit) whether it ran alone or in a mix of different grid sizes,
+and matches the fp64 oracle (relative L2 <= 2e-5 on the traces, the fp32 bar);
+admission respects the HBM budget; over-budget requests are rejected; polls
+time out; a shot that goes non-finite reports it without touching the others."""
 import time
 
 import numpy as np
@@ -13,9 +15,12 @@ from gpu_util import ensure_lib
 
 pytestmark = pytest.mark.gpu
 
-# (inner nx, ny, nz, nb, nt, seed)
+# (inner nx, ny, nz, nb, nt, seed); the last is the serving mix's smallest grid
+# (128^3 computed, PML 16) at a reduced step count, so the multi-shot kernel's
+# tiles, z chunks and shot table are exercised at a size the server serves
 MIX = [(24, 24, 24, 6, 90, 1), (40, 28, 20, 8, 150, 2), (18, 36, 30, 4, 60, 3),
-       (32, 32, 32, 6, 120, 4), (20, 20, 44, 5, 70, 5), (48, 40, 24, 8, 100, 6)]
+       (32, 32, 32, 6, 120, 4), (20, 20, 44, 5, 70, 5), (48, 40, 24, 8, 100, 6),
+       (96, 96, 96, 16, 60, 7)]
 
 
 def _request(case):
@@ -38,6 +43,12 @@ def _alone(g, vel, wav, nt, src, rec):
     return tr
 
 
+def _oracle_traces(g, vel, wav, nt, src, rec):
+    go = oracle.Grid(g.nx, g.ny, g.nz, g.nb, g.dx, g.dy, g.dz, g.dt, vmax=g.vmax,
+                     r0=float(np.float32(g.pml_r0)))
+    return oracle.run_shot(go, vel, wav, nt, src, rec, want_state=False)["traces"]
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _lib():
     ensure_lib()
@@ -46,6 +57,11 @@ def _lib():
 def test_results_equal_run_shot_alone_and_in_mix():
     reqs = [_request(c) for c in MIX]
     ref = [_alone(*r) for r in reqs]
+    for case, r, want in zip(MIX, reqs, ref):
+        ora = _oracle_traces(*r)
+        assert np.abs(ora).max() > 0
+        e = float(np.linalg.norm(want - ora) / np.linalg.norm(ora))
+        assert e <= 2e-5, (case, e)
     for slots in (1, 16):  # one at a time, then all in the mix
         with seisgb.Server(8 << 30, max_slots=slots, steps_per_graph=16) as sv:
             tickets = []
@@ -104,3 +120,29 @@ def test_poll_timeout_then_result():
         assert np.array_equal(tr, _alone(*r))
         with pytest.raises(seisgb.SeisgbError):
             sv.poll(t, r[3], r[5].shape[0])  # consumed ticket is unknown now
+
+
+def test_nonfinite_shot_reported_alone_in_the_mix():
+    """A request whose wavelet drives its field to Inf (fp32 overflow, no device
+    fault) ends with SGB_ERR_NONFINITE; requests served beside it finish OK with
+    the same traces as alone: each shot has its own device error word."""
+    good = [_request(c) for c in MIX[:3]]
+    # 1 m spacing and a wavelet near the fp32 maximum: the field reaches Inf
+    # within a few steps (the run_shot NONFINITE case)
+    dt = float(np.float32(0.4 * oracle.cfl_dt(2500.0, 1.0, 1.0, 1.0)))
+    g = seisgb.make_grid(12, 12, 12, 3, 1.0, 1.0, 1.0, dt, 2500.0)
+    nt = 40
+    bad = (g, np.full(g.shape, 2500.0, np.float32), np.full(nt, 3e38, np.float32), nt,
+           (9, 9, 9), np.array([[9, 9, 9]], np.int32))
+    with seisgb.Server(8 << 30, max_slots=8, steps_per_graph=8) as sv:
+        order = good[:2] + [bad] + good[2:]
+        tickets = [sv.submit(*r) for r in order]
+        for i, (t, r) in enumerate(zip(tickets, order)):
+            rc, res, tr = sv.poll(t, r[3], r[5].shape[0], timeout_us=60_000_000)
+            assert rc == seisgb.OK
+            if i == 2:
+                assert res.status == seisgb.ERR_NONFINITE
+                assert not np.isfinite(tr).all()
+            else:
+                assert res.status == seisgb.OK, i
+                assert np.array_equal(tr, _alone(*r)), i
