@@ -350,6 +350,80 @@ def _gradient(a, seisgb, synth, peak):
                         "central differences: tests"}
 
 
+def _stencil_step_ms(g, fmt, seisgb, dev, d_v, dt, src, d_w, launches, nt):
+    """Mean time of one stencil_step launch on 16-bit fields (back to back, CUDA
+    events on the launching stream), the per-launch unit of the roofline."""
+    import torch
+    L = seisgb.layout(g)
+    tdt = torch.float16 if fmt == seisgb.FP16_SCALED else torch.bfloat16
+    u = [torch.zeros(int(L.elems), dtype=tdt, device=dev) for _ in range(2)]
+    phi = torch.zeros(int(L.elems), dtype=torch.float32, device=dev)
+    d_m = torch.zeros(int(L.elems), dtype=torch.float32, device=dev)
+    g32 = seisgb.make_grid(g.nx, g.ny, g.nz, g.nb, g.dx, g.dy, g.dz, g.dt, g.vmax)
+    seisgb.pack(g32, (d_v * dt) ** 2, d_m)
+    scale = torch.tensor([1.0] * 4 + [0.0] * 4, dtype=torch.float32, device=dev)
+    sc = scale if fmt == seisgb.FP16_SCALED else None
+    for n in range(3):
+        seisgb.stencil_step(g, u[n % 2], u[(n + 1) % 2], d_m, phi, n, source=(*src, d_w),
+                            scale_state=sc)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for n in range(launches):
+        seisgb.stencil_step(g, u[n % 2], u[(n + 1) % 2], d_m, phi, (n + 3) % nt,
+                            source=(*src, d_w), scale_state=sc)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    seisgb.device_status()
+    return r0.elapsed_time(r1) / launches
+
+
+def _temporal(a, seisgb, w, vel, vmax, dt, src, rec, d_v, d_w, d_tr, dev, barrier, single, world):
+    """run_shot with time_block 2 on the benchmark workload (CUDA events around
+    a.steps shots after one warm-up shot) and the mean time of one
+    stencil_step2 pair (back to back)."""
+    import torch
+    from paper_2009_04619_gb300 import replicas
+    g2 = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, time_block=2)
+    seisgb.run_shot(g2, d_v, d_w, w.nt, src, rec, d_tr)
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        seisgb.run_shot(g2, d_v, d_w, w.nt, src, rec, d_tr)
+    e1.record(stream)
+    barrier()
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), device=dev) / a.steps
+    val = w.points * w.nt * world / (ms / 1e3) / 1e9
+    L = seisgb.layout(g2)
+    f = [torch.zeros(int(L.elems), dtype=torch.float32, device=dev) for _ in range(6)]
+    seisgb.pack(g2, (d_v * dt) ** 2, f[4])
+    M = max(10, a.roofline_launches // 4)
+    for k in range(3):
+        p = k % 2
+        seisgb.stencil_step2(g2, f[2 * p], f[2 * p + 1], f[2 - 2 * p], f[3 - 2 * p], f[4], f[5],
+                             2 * k, source=(*src, d_w))
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for k in range(M):
+        p = k % 2
+        seisgb.stencil_step2(g2, f[2 * p], f[2 * p + 1], f[2 - 2 * p], f[3 - 2 * p], f[4], f[5],
+                             (2 * k) % (w.nt - 1), source=(*src, d_w))
+    r1.record(stream)
+    torch.cuda.synchronize()
+    seisgb.device_status()
+    pair_ms = r0.elapsed_time(r1) / M
+    del f
+    return {"value": val, "unit": UNIT, "ms_per_shot": ms, "vs_single_step": val / single,
+            "pair_ms": pair_ms, "ms_per_step_in_pairs": pair_ms / 2,
+            "default": "off (time_block 0); results are bit-identical either way",
+            "design": "two-step kernel on the inner region shrunk by 4 points, two single-step "
+                      "shell launches on the rest"}
+
+
 def _small_case(a, seisgb, synth, dev, barrier):
     """Gpt/s of the small forward-modelling case (64^3 inner + 16-point PML,
     constant 2000 m/s, 100 steps) through run_shot, device-resident inputs,
@@ -533,12 +607,24 @@ def main():
         barrier()
         pms = replicas.max_over_ranks(p0.elapsed_time(p1), device=dev) / a.steps
         alg16 = _alg_bytes_per_launch(w, wave_bytes=2)
+        kms = _stencil_step_ms(g=gp, fmt=fmt, seisgb=seisgb, dev=dev, d_v=d_v, dt=dt, src=src,
+                               d_w=d_w, launches=M, nt=w.nt)
         precision[fname] = {
             "value": w.points * w.nt * world / (pms / 1e3) / 1e9, "unit": UNIT,
             "ms_per_step": pms, "alg_bytes_per_launch": alg16,
             "achieved_gbs": alg16 / (pms / w.nt / 1e3) / 1e9,
             "frac": alg16 / (pms / w.nt / 1e3) / 1e9 / peak,
+            "vs_fp32": (w.points * w.nt * world / (pms / 1e3) / 1e9) / value,
+            "roofline": {"bound": "hbm", "kernel": "fused_step_kernel (stencil_step)",
+                         "kernel_ms": kms, "achieved": alg16 / (kms / 1e3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": alg16 / (kms / 1e3) / 1e9 / peak,
+                         "alg_bytes_per_launch": alg16},
             "error": "relative L2 vs the fp64 oracle: see the 256^3 x 1000-step precision test"}
+
+    # temporal blocking: the same shot with time_block 2 (two steps per HBM
+    # pass on the PML-free interior, identical results), and the pair unit
+    temporal = _temporal(a, seisgb, w, vel, vmax, dt, src, rec, d_v, d_w, d_tr, dev, barrier,
+                         value, world)
 
     # the small forward-modelling case (64^3 inner + 16-point PML, 100 steps):
     # whole shots through run_shot, device-resident inputs (its four fields fit
@@ -566,6 +652,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "precision": precision,
+        "temporal_blocking": temporal,
         "small_case": small,
         "serving": serving,
         "gradient": gradient,

@@ -58,6 +58,12 @@ typedef struct {
     float pml_r0;        /* PML target reflection coefficient in (0, 1];
                             1 switches the damping off */
     int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED or SGB_BF16 */
+    int32_t time_block;  /* run_shot's time steps per pass over HBM: 0 or 1 (one
+                            fused step per launch), or 2 (temporal blocking:
+                            two steps per pass on the PML-free interior, see
+                            stencil_step2; SGB_FP32 storage only).  The result
+                            is the same bits either way.  Other entry points
+                            ignore it. */
 } sgb_grid;
 
 /* Padded device layout of one field (element counts; multiply by the element
@@ -100,7 +106,10 @@ int sgb_cfl_dt(const sgb_grid *g, float vmax, float *dt_max);
  * u_prev_to_next with u^{n+1} (the update is pointwise in u^{n-1}, so this is
  * safe).  m = V^2 dt^2 (fp32, padded layout).  phi: the PML auxiliary field,
  * fp32 padded layout, read and written at PML points only (start from zeros).
- * u fields are fp32 (storage SGB_FP32).  step selects src->wavelet[step].
+ * The u fields hold g->storage elements in the padded layout: fp32
+ * (SGB_FP32) or bf16 (SGB_BF16, stored with stochastic rounding, arithmetic
+ * in fp32); SGB_FP16_SCALED fields go through stencil_step_scaled (INVALID_ARG
+ * here).  step selects src->wavelet[step].
  * src and rec may be NULL.  All device pointers must be 16-byte aligned.
  * Asynchronous on stream.  UNSTABLE_DT when g->dt exceeds the CFL limit for
  * g->vmax.  A bounded kernel wait that gave up or a non-finite receiver sample
@@ -109,6 +118,40 @@ int sgb_cfl_dt(const sgb_grid *g, float vmax, float *dt_max);
 int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next, const float *m,
                  float *phi, int32_t step, const sgb_source *src, const sgb_receivers *rec,
                  void *stream);
+
+/* stencil_step for fp16 wavefields with a per-field power-of-two scale
+ * (g->storage == SGB_FP16_SCALED; the paper fixes no precision, this is the
+ * reduced-precision storage form of the same step).  A stored value is u / s.
+ * scale_state: device float[8], 16-byte aligned, owned by the caller:
+ * [0..3] = s of u^k at index k & 3, [4..7] = max |u^k| at index k & 3.  The
+ * step for `step` = n reads s and max of u^n and u^{n-1}, picks s of u^{n+1}
+ * (the power of two that keeps 4 max(max|u^n|, max|u^{n-1}|) plus the
+ * injected amplitude below 2^14 s), writes it to [(n+1) & 3], zeroes
+ * [4 + ((n+2) & 3)] and accumulates max |u^{n+1}| into [4 + ((n+1) & 3)].
+ * Start a run from zero fields with {1, 1, 1, 1, 0, 0, 0, 0}.  Receivers
+ * sample u^{n+1} times its scale.  Otherwise as stencil_step. */
+int stencil_step_scaled(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
+                        const float *m, float *phi, float *scale_state, int32_t step,
+                        const sgb_source *src, const sgb_receivers *rec, void *stream);
+
+/* Two time steps, n and n + 1, with temporal blocking (the 3.5D blocking
+ * that the paper names as future work, section VI): on the box B = the inner
+ * region shrunk by the stencil radius on every side (x bounds rounded inwards
+ * to multiples of 4) one kernel reads u^{n-1}, u^n and m once and writes
+ * u^{n+1} and u^{n+2} (the first step evaluated on each tile plus a radius-4
+ * halo, the second on the tile); the rest of the grid (the PML and the inner
+ * band next to it) takes two ordinary fused steps (Eq. 2 and the PML update,
+ * phi updated in place).  The results are bit-identical to two stencil_step
+ * calls.  All fields fp32 in the padded layout (storage SGB_FP32), 16-byte
+ * aligned; u_prev = u^{n-1}, u_cur = u^n are read, u_next = u^{n+1} and
+ * u_next2 = u^{n+2} written: four distinct buffers (INVALID_ARG when an
+ * output overlaps an input, another output or phi).  src->wavelet[step] and
+ * [step + 1] are injected.  No receivers (gather them from u_next and
+ * u_next2).  Three launches on stream, asynchronous; errors are recorded in
+ * the device error word of stencil_step (sgb_device_status). */
+int stencil_step2(const sgb_grid *g, const float *u_prev, const float *u_cur, float *u_next,
+                  float *u_next2, const float *m, float *phi, int32_t step,
+                  const sgb_source *src, void *stream);
 
 /* A whole shot (Algorithm 1): u^0 = u^{-1} = 0, nt steps, source injection and
  * receiver sampling every step.

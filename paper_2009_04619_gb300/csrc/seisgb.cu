@@ -18,6 +18,7 @@
 #include "aux_kernels.cuh"
 #include "step_kernel.cuh"
 #include "step_config.cuh"
+#include "two_step.cuh"
 
 using namespace sgb;
 
@@ -175,6 +176,10 @@ int check_grid(const sgb_grid *g, sgb_layout_info *L)
         return fail(SGB_ERR_INVALID_ARG, "pml_r0 must be in (0, 1] (got %g)", (double)g->pml_r0);
     if (g->storage != SGB_FP32 && g->storage != SGB_FP16_SCALED && g->storage != SGB_BF16)
         return fail(SGB_ERR_INVALID_ARG, "unknown storage format %d", g->storage);
+    if (g->time_block < 0 || g->time_block > 2)
+        return fail(SGB_ERR_INVALID_ARG, "time_block must be 0, 1 or 2 (got %d)", g->time_block);
+    if (g->time_block == 2 && g->storage != SGB_FP32)
+        return fail(SGB_ERR_INVALID_ARG, "time_block 2 needs SGB_FP32 storage");
     compute_layout(g, L);
     if (L->elems > (int64_t(1) << 40)) return fail(SGB_ERR_INVALID_ARG, "field too large");
     return SGB_OK;
@@ -522,18 +527,71 @@ extern "C" int sgb_device_status(void *stream)
     return dev_err_status(v);
 }
 
-extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
-                            const float *m, float *phi, int32_t step, const sgb_source *src,
-                            const sgb_receivers *rec, void *stream)
+namespace {
+
+// One step of storage type T on caller-owned fields (stencil_step and
+// stencil_step_scaled after their argument checks).
+template <class T>
+int stencil_step_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
+                   const void *u_cur, void *u_out, const float *m, float *phi, ScaleState *scale,
+                   int32_t step, const sgb_source *src, const sgb_receivers *rec)
+{
+    int rc;
+    StepArgs a;
+    fill_step_constants(g, L, a);
+    a.u_out = u_out;
+    a.u_cur = u_cur;
+    a.phi = phi;
+    a.err = ds->err;
+    a.step_add = step;
+    a.scale = scale;
+    if (src) {
+        a.si = src->i;
+        a.sj = src->j;
+        a.sk = src->k;
+        a.wavelet = src->wavelet;
+        a.m_src = m + L.origin + (long long)src->k * L.stride_z + (long long)src->j * L.sx + src->i;
+    }
+    const int occ = std::is_same<T, float>::value ? ds->occ
+                    : std::is_same<T, __half>::value ? ds->occ_h : ds->occ_b;
+    int grid = 0;
+    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, occ, a, &grid);
+    StepMaps mp;
+    if ((rc = encode_step_maps<T>(mp, a.u_cur, a.u_out, m, phi, L))) return rc;
+    if ((rc = launch_step<T>(a, mp, grid, st))) return rc;
+    if (rec && rec->nrec > 0) {
+        std::vector<long long> off(rec->nrec);
+        for (int r = 0; r < rec->nrec; ++r)
+            off[r] = L.origin + (long long)rec->ijk[3 * r + 2] * L.stride_z +
+                     (long long)rec->ijk[3 * r + 1] * L.sx + rec->ijk[3 * r];
+        void *d_off = nullptr;
+        Scratch sc{st, ds->pool, {}};
+        if ((rc = sc.get(&d_off, off.size() * sizeof(long long)))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(long long),
+                                 cudaMemcpyHostToDevice, st));
+        // u^{n+1} times its scale (fp16: s[(step + 1) & 3], written by the step)
+        gather_t_kernel<T><<<(rec->nrec + 255) / 256, 256, 0, st>>>(
+            static_cast<const T *>(u_out), static_cast<const long long *>(d_off), rec->nrec,
+            scale ? &scale->s[(step + 1) & 3] : nullptr, rec->traces, ds->err);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+        // the pageable copy above is staged before cudaMemcpyAsync returns; the
+        // scratch is released stream-ordered after the gather
+    }
+    return SGB_OK;
+}
+
+int stencil_step_common(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
+                        const float *m, float *phi, float *scale, int32_t step,
+                        const sgb_source *src, const sgb_receivers *rec, void *stream)
 {
     sgb_layout_info L;
     int rc = check_grid(g, &L);
     if (rc) return rc;
-    if (g->storage != SGB_FP32)
-        return fail(SGB_ERR_INVALID_ARG, "stencil_step: only SGB_FP32 storage here");
     if (!u_cur || !u_prev_to_next || !m) return fail(SGB_ERR_INVALID_ARG, "NULL field pointer");
     if (g->nb > 0 && !phi) return fail(SGB_ERR_INVALID_ARG, "phi is required when nb > 0");
-    if (!aligned16(u_cur) || !aligned16(u_prev_to_next) || !aligned16(m) || (phi && !aligned16(phi)))
+    if (!aligned16(u_cur) || !aligned16(u_prev_to_next) || !aligned16(m) || (phi && !aligned16(phi)) ||
+        (scale && !aligned16(scale)))
         return fail(SGB_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (u_cur == u_prev_to_next) return fail(SGB_ERR_INVALID_ARG, "u_cur aliases u_prev_to_next");
     if (step < 0) return fail(SGB_ERR_INVALID_ARG, "step must be >= 0");
@@ -556,47 +614,215 @@ extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_t
     DevState *ds;
     if ((rc = device_state(&ds))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    ScaleState *ss = reinterpret_cast<ScaleState *>(scale);
+    switch (g->storage) {
+    case SGB_FP16_SCALED:
+        return stencil_step_t<__half>(g, L, ds, st, u_cur, u_prev_to_next, m, phi, ss, step, src, rec);
+    case SGB_BF16:
+        return stencil_step_t<__nv_bfloat16>(g, L, ds, st, u_cur, u_prev_to_next, m, phi, nullptr,
+                                             step, src, rec);
+    default:
+        return stencil_step_t<float>(g, L, ds, st, u_cur, u_prev_to_next, m, phi, nullptr, step,
+                                     src, rec);
+    }
+}
 
-    StepArgs a;
-    fill_step_constants(g, L, a);
-    a.u_out = u_prev_to_next;
-    a.u_cur = u_cur;
-    a.phi = phi;
-    a.err = ds->err;
-    a.step_add = step;
-    if (src) {
-        a.si = src->i;
-        a.sj = src->j;
-        a.sk = src->k;
-        a.wavelet = src->wavelet;
-    }
-    int grid = 0;
-    choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, ds->occ, a, &grid);
-    StepMaps mp;
-    if ((rc = encode_step_maps<float>(mp, a.u_cur, a.u_out, m, phi, L))) return rc;
-    if ((rc = launch_step<float>(a, mp, grid, st))) return rc;
-    if (rec && rec->nrec > 0) {
-        std::vector<long long> off(rec->nrec);
-        for (int r = 0; r < rec->nrec; ++r)
-            off[r] = L.origin + (long long)rec->ijk[3 * r + 2] * L.stride_z +
-                     (long long)rec->ijk[3 * r + 1] * L.sx + rec->ijk[3 * r];
-        void *d_off = nullptr;
-        Scratch sc{st, ds->pool, {}};
-        if ((rc = sc.get(&d_off, off.size() * sizeof(long long)))) return rc;
-        CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(long long),
-                                 cudaMemcpyHostToDevice, st));
-        gather_kernel<<<(rec->nrec + 255) / 256, 256, 0, st>>>(
-            static_cast<const float *>(u_prev_to_next), static_cast<const long long *>(d_off),
-            rec->nrec, rec->traces, ds->err);
-        CUDA_TRY(cudaGetLastError());
-        ++t_launches;
-        // the pageable copy above is staged before cudaMemcpyAsync returns; the
-        // scratch is released stream-ordered after the gather
-    }
-    return SGB_OK;
+}  // namespace
+
+extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
+                            const float *m, float *phi, int32_t step, const sgb_source *src,
+                            const sgb_receivers *rec, void *stream)
+{
+    if (g && g->storage == SGB_FP16_SCALED)
+        return fail(SGB_ERR_INVALID_ARG,
+                    "stencil_step: SGB_FP16_SCALED fields carry a scale state; use stencil_step_scaled");
+    return stencil_step_common(g, u_cur, u_prev_to_next, m, phi, nullptr, step, src, rec, stream);
+}
+
+extern "C" int stencil_step_scaled(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
+                                   const float *m, float *phi, float *scale_state, int32_t step,
+                                   const sgb_source *src, const sgb_receivers *rec, void *stream)
+{
+    if (!g || g->storage != SGB_FP16_SCALED)
+        return fail(SGB_ERR_INVALID_ARG, "stencil_step_scaled: storage must be SGB_FP16_SCALED");
+    if (!scale_state) return fail(SGB_ERR_INVALID_ARG, "stencil_step_scaled: scale_state is NULL");
+    return stencil_step_common(g, u_cur, u_prev_to_next, m, phi, scale_state, step, src, rec,
+                               stream);
 }
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// Temporally blocked pairs of steps (time_block 2, stencil_step2)
+// ---------------------------------------------------------------------------
+using TCfg = TwoCfg<56, 16, 8, 8, 6>;
+
+// Work of one pair (steps n, n+1): the two-step kernel on the box B (the inner
+// region shrunk by the stencil radius, x bounds on multiples of 4) and two
+// single-step shell launches on the standard tiles that reach outside B.
+struct PairPlan {
+    bool box = false;
+    int bx0 = 0, bx1 = 0, by0 = 0, by1 = 0, bz0 = 0, bz1 = 0;
+    int tiles_x = 0, tiles_y = 0, zc = 0, grid = 0;
+    std::vector<int4> shell;
+};
+
+int two_step_prepared = 0;
+
+int prepare_two_step()
+{
+    if (two_step_prepared) return SGB_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    CUDA_TRY(cudaFuncSetAttribute(two_step_kernel<TCfg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TCfg::SMEM_BYTES));
+    CUDA_TRY(cudaFuncSetAttribute(shell_step_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Stage<Cfg, float>::SMEM_BYTES));
+    two_step_prepared = 1;
+    return SGB_OK;
+}
+
+void plan_pair(const sgb_grid *g, const sgb_layout_info &L, const DevState &ds, PairPlan &pp)
+{
+    const int nb = g->nb;
+    pp.bx0 = (nb + R + 3) / 4 * 4;
+    pp.bx1 = (nb + g->nx - R) / 4 * 4;
+    pp.by0 = nb + R;
+    pp.by1 = nb + g->ny - R;
+    pp.bz0 = nb + R;
+    pp.bz1 = nb + g->nz - R;
+    pp.box = pp.bx1 > pp.bx0 && pp.by1 > pp.by0 && pp.bz1 > pp.bz0;
+    if (!pp.box) pp.bx0 = pp.bx1 = pp.by0 = pp.by1 = pp.bz0 = pp.bz1 = 0;
+    if (pp.box) {
+        pp.tiles_x = (pp.bx1 - pp.bx0 + TCfg::BX - 1) / TCfg::BX;
+        pp.tiles_y = (pp.by1 - pp.by0 + TCfg::BY - 1) / TCfg::BY;
+        // z-chunks: fewest waves x (chunk + the 8 planes of step-1 overhead),
+        // chunks of at most 64 planes (neighbouring CTAs stay close in z)
+        const int nzb = pp.bz1 - pp.bz0;
+        const long long tiles = (long long)pp.tiles_x * pp.tiles_y, slots = ds.sms;
+        double best = 1e300;
+        pp.zc = nzb;
+        for (int c = 1; c <= nzb; ++c) {
+            const int zc = (nzb + c - 1) / c;
+            if (zc > 64) continue;
+            const long long units = tiles * ((nzb + zc - 1) / zc);
+            const double cost = (double)((units + slots - 1) / slots) * (zc + 2 * R);
+            if (cost < best * 0.999) {
+                best = cost;
+                pp.zc = zc;
+            }
+            if (zc <= 8) break;
+        }
+        pp.grid = (int)(tiles * ((nzb + pp.zc - 1) / pp.zc));
+    }
+    // shell: standard tiles; those inside B's x-y extent only need the z ranges
+    // outside it; units sorted by z so that CTAs running together share planes
+    pp.shell.clear();
+    const int zs = 32;
+    for (int y = 0; y < L.Ny; y += Cfg::BY)
+        for (int x = 0; x < L.Nx; x += Cfg::BX) {
+            const int xe = std::min(x + Cfg::BX, L.Nx), ye = std::min(y + Cfg::BY, L.Ny);
+            const bool inside = pp.box && x >= pp.bx0 && xe <= pp.bx1 && y >= pp.by0 && ye <= pp.by1;
+            int ranges[2][2] = {{0, inside ? pp.bz0 : L.Nz}, {inside ? pp.bz1 : L.Nz, L.Nz}};
+            for (auto &r : ranges) {
+                const int len = r[1] - r[0];
+                if (len <= 0) continue;
+                const int nch = (len + zs - 1) / zs, zc = (len + nch - 1) / nch;
+                for (int z = r[0]; z < r[1]; z += zc) pp.shell.push_back(make_int4(x, y, z, std::min(z + zc, r[1])));
+            }
+        }
+    std::stable_sort(pp.shell.begin(), pp.shell.end(), [](const int4 &a, const int4 &b) {
+        return a.z != b.z ? a.z < b.z : (a.y != b.y ? a.y < b.y : a.x < b.x);
+    });
+}
+
+// Tensor maps of one pair: (u^{n-1}, u^n) -> (u^{n+1}, u^{n+2}).
+struct PairMaps {
+    CUtensorMap two_u, two_up, two_m;  // the two-step kernel's u^n box, u^{n-1} and m tiles
+    StepMaps shell0, shell1;           // shell launches of steps n and n+1
+};
+
+int encode_pair_maps(PairMaps &pm, const float *a_prev, const float *b_cur, const float *c_next,
+                     const float *m, const float *phi, const sgb_layout_info &L)
+{
+    int rc;
+    if ((rc = encode_map<float>(&pm.two_u, b_cur, L, TCfg::UW, TCfg::UH, SGB_L2PROMO))) return rc;
+    if ((rc = encode_map<float>(&pm.two_up, a_prev, L, TCfg::EX, TCfg::EY))) return rc;
+    if ((rc = encode_map<float>(&pm.two_m, m, L, TCfg::EX, TCfg::EY))) return rc;
+    if ((rc = encode_step_maps<float>(pm.shell0, b_cur, a_prev, m, phi, L))) return rc;
+    if ((rc = encode_step_maps<float>(pm.shell1, c_next, b_cur, m, phi, L))) return rc;
+    return SGB_OK;
+}
+
+// Enqueue the three launches of one pair.  base: the step constants with phi,
+// error word, source, receivers (sampled by the shell launches from their
+// u^n, rows n-1 and n).  Steps n = *step_ptr + step_add and n + 1.
+int launch_pair(const sgb_grid *g, const PairPlan &pp, const PairMaps &pm, const int4 *d_units,
+                const StepArgs &base, float *c_next, float *d_next2, const float *b_cur,
+                const int *step_ptr, int step_add, cudaStream_t st)
+{
+    if (pp.box) {
+        TwoStepArgs t;
+        memset(&t, 0, sizeof t);
+        t.out1 = c_next;
+        t.out2 = d_next2;
+        t.Nx = base.Nx;
+        t.Ny = base.Ny;
+        t.Nz = base.Nz;
+        t.sx = base.sx;
+        t.sxy = base.sxy;
+        t.origin = base.origin;
+        t.c0 = base.c0;
+        for (int q = 0; q < 4; ++q) {
+            t.cx[q] = base.cx[q];
+            t.cy[q] = base.cy[q];
+            t.cz[q] = base.cz[q];
+        }
+        t.bx0 = pp.bx0;
+        t.bx1 = pp.bx1;
+        t.by0 = pp.by0;
+        t.by1 = pp.by1;
+        t.bz0 = pp.bz0;
+        t.bz1 = pp.bz1;
+        t.tiles_x = pp.tiles_x;
+        t.tiles_y = pp.tiles_y;
+        t.zc = pp.zc;
+        t.si = base.si;
+        t.sj = base.sj;
+        t.sk = base.sk;
+        t.wavelet = base.wavelet;
+        t.inv_vol = base.inv_vol;
+        t.step_ptr = step_ptr;
+        t.step_add = step_add;
+        t.err = base.err;
+        two_step_kernel<TCfg><<<pp.grid, TCfg::BLOCK, TCfg::SMEM_BYTES, st>>>(t, pm.two_u, pm.two_up,
+                                                                              pm.two_m);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+    }
+    const int nunits = (int)pp.shell.size();
+    if (nunits == 0) return SGB_OK;
+    for (int h = 0; h < 2; ++h) {
+        StepArgs a = base;
+        a.units = d_units;
+        a.bx0 = pp.bx0;
+        a.bx1 = pp.bx1;
+        a.by0 = pp.by0;
+        a.by1 = pp.by1;
+        a.bz0 = pp.bz0;
+        a.bz1 = pp.bz1;
+        a.u_cur = h == 0 ? b_cur : c_next;
+        a.u_out = h == 0 ? c_next : d_next2;
+        a.step_ptr = step_ptr;
+        a.step_add = step_add + h;
+        const StepMaps &mp = h == 0 ? pm.shell0 : pm.shell1;
+        shell_step_kernel<Cfg><<<nunits, Cfg::BLOCK, Stage<Cfg, float>::SMEM_BYTES, st>>>(
+            a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+    }
+    (void)g;
+    return SGB_OK;
+}
 
 // Shot time loop and outputs for wavefield storage T (run_shot after its
 // argument checks and the CFL check).
@@ -727,7 +953,200 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     return SGB_OK;
 }
 
+// run_shot with time_block 2 (fp32): steps in temporally blocked pairs, an
+// odd last step as one ordinary fused step.  Four wavefield buffers: a pair
+// reads (u^{n-1}, u^n) from one two and writes (u^{n+1}, u^{n+2}) to the other.
+int run_shot_pairs(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
+                   Scratch &sc, const float *d_vel, const float *d_wav, int nt,
+                   const int32_t *src_ijk, int nrec, const long long *d_off, float *d_tr,
+                   float *final_u, int *d_err)
+{
+    int rc;
+    if ((rc = prepare_two_step())) return rc;
+    const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
+    const size_t fbytes = (size_t)L.elems * 4;
+    float *u[4], *phi, *m;
+    int *d_step;
+    for (int q = 0; q < 4; ++q)
+        if ((rc = sc.get((void **)&u[q], fbytes))) return rc;
+    if ((rc = sc.get((void **)&phi, fbytes)) || (rc = sc.get((void **)&m, fbytes)) ||
+        (rc = sc.get((void **)&d_step, sizeof(int))))
+        return rc;
+    CUDA_TRY(cudaMemsetAsync(d_step, 0, sizeof(int), st));
+    for (int q = 0; q < 2; ++q) CUDA_TRY(cudaMemsetAsync(u[q], 0, fbytes, st));
+    CUDA_TRY(cudaMemsetAsync(phi, 0, fbytes, st));
+    CUDA_TRY(cudaMemsetAsync(m, 0, fbytes, st));
+    make_m_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), d_vel, g->dt, m);
+    CUDA_TRY(cudaGetLastError());
+    ++t_launches;
+
+    StepArgs base;
+    fill_step_constants(g, L, base);
+    base.phi = phi;
+    base.err = d_err;
+    if (src_ijk) {
+        base.si = src_ijk[0];
+        base.sj = src_ijk[1];
+        base.sk = src_ijk[2];
+        base.wavelet = d_wav;
+    }
+    base.nrec = nrec;
+    base.rec_off = d_off;
+    base.traces = d_tr;
+    PairPlan pp;
+    plan_pair(g, L, *ds, pp);
+    int4 *d_units = nullptr;
+    if (!pp.shell.empty()) {
+        if ((rc = sc.get((void **)&d_units, pp.shell.size() * sizeof(int4)))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(d_units, pp.shell.data(), pp.shell.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, st));
+    }
+    // pair parity p: reads (u[2p], u[2p+1]) = (u^{n-1}, u^n), writes u[2(1-p)],
+    // u[2(1-p)+1]
+    PairMaps pm[2];
+    for (int p = 0; p < 2; ++p)
+        if ((rc = encode_pair_maps(pm[p], u[2 * p], u[2 * p + 1], u[2 * (1 - p)], m, phi, L)))
+            return rc;
+    auto pair = [&](int parity, const int *step_ptr, int step_add, cudaStream_t s2) {
+        return launch_pair(g, pp, pm[parity], d_units, base, u[2 * (1 - parity)],
+                           u[2 * (1 - parity) + 1], u[2 * parity + 1], step_ptr, step_add, s2);
+    };
+
+    const int GS = 32;  // steps per graph replay: 16 pairs (even: the parity repeats)
+    const int replays = nt / GS;
+    if (replays > 0) {
+        cudaStream_t cs;
+        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int crc = SGB_OK;
+        const int64_t before = t_launches;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            for (int j = 0; j < GS / 2 && crc == SGB_OK; ++j) crc = pair(j & 1, d_step, 2 * j, cs);
+            if (crc == SGB_OK) {
+                advance_kernel<<<1, 32, 0, cs>>>(d_step, GS);
+                ce = cudaGetLastError();
+            }
+            cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+            if (ce == cudaSuccess) ce = ee;
+        }
+        const int64_t per_replay = t_launches - before + 1;
+        t_launches = before;  // captured launches are counted at replay
+        if (ce == cudaSuccess && crc == SGB_OK) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce == cudaSuccess && crc == SGB_OK) {
+            for (int r = 0; r < replays && ce == cudaSuccess; ++r) {
+                ce = cudaGraphLaunch(exec, st);
+                t_launches += per_replay;
+            }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (crc) return crc;
+        CUDA_TRY(ce);
+    }
+    int n = replays * GS;
+    for (; n + 1 < nt; n += 2)
+        if ((rc = pair((n / 2) & 1, nullptr, n, st))) return rc;
+    // (u^{n-1}, u^n) now live in u[2p], u[2p+1], p = (n / 2) & 1
+    const int par = (n / 2) & 1;
+    float *u_final_dev = u[2 * par + 1];
+    if (n < nt) {  // odd step count: one ordinary fused step, in place over u^{n-1}
+        StepArgs a = base;
+        a.u_out = u[2 * par];
+        a.u_cur = u[2 * par + 1];
+        a.step_add = n;
+        int grid = 0;
+        choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, ds->occ, a, &grid);
+        StepMaps mp;
+        if ((rc = encode_step_maps<float>(mp, a.u_cur, a.u_out, m, phi, L))) return rc;
+        if ((rc = launch_step<float>(a, mp, grid, st))) return rc;
+        u_final_dev = u[2 * par];
+    }
+    if (nrec > 0 && nt > 0) {
+        gather_t_kernel<float><<<(nrec + 255) / 256, 256, 0, st>>>(
+            u_final_dev, d_off, nrec, nullptr, d_tr + (size_t)(nt - 1) * nrec, d_err);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+    }
+    if (final_u) {
+        const bool host_u = !is_device_ptr(final_u);
+        float *dst = final_u;
+        if (host_u && (rc = sc.get((void **)&dst, (size_t)ncomp * 4))) return rc;
+        unpack_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), u_final_dev, dst);
+        CUDA_TRY(cudaGetLastError());
+        ++t_launches;
+        if (host_u)
+            CUDA_TRY(cudaMemcpyAsync(final_u, dst, (size_t)ncomp * 4, cudaMemcpyDeviceToHost, st));
+    }
+    return SGB_OK;
+}
+
 }  // namespace
+
+extern "C" int stencil_step2(const sgb_grid *g, const float *u_prev, const float *u_cur,
+                             float *u_next, float *u_next2, const float *m, float *phi,
+                             int32_t step, const sgb_source *src, void *stream)
+{
+    sgb_layout_info L;
+    int rc = check_grid(g, &L);
+    if (rc) return rc;
+    if (g->storage != SGB_FP32) return fail(SGB_ERR_INVALID_ARG, "stencil_step2: SGB_FP32 storage only");
+    const float *f[4] = {u_prev, u_cur, u_next, u_next2};
+    for (int q = 0; q < 4; ++q) {
+        if (!f[q]) return fail(SGB_ERR_INVALID_ARG, "NULL field pointer");
+        if (!aligned16(f[q])) return fail(SGB_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    }
+    if (!m || !aligned16(m) || (phi && !aligned16(phi)))
+        return fail(SGB_ERR_INVALID_ARG, "m (and phi) must be non-NULL and 16-byte aligned");
+    if (g->nb > 0 && !phi) return fail(SGB_ERR_INVALID_ARG, "phi is required when nb > 0");
+    {
+        const size_t fb = (size_t)L.elems * 4;
+        const Span ins[] = {{u_prev, fb, "u_prev"}, {u_cur, fb, "u_cur"}, {m, fb, "m"}};
+        const Span outs[] = {{u_next, fb, "u_next"}, {u_next2, fb, "u_next2"}, {phi, fb, "phi"}};
+        if ((rc = check_no_overlap(outs, 3, ins, 3))) return rc;
+        if (spans_overlap(ins[0], ins[1])) return fail(SGB_ERR_INVALID_ARG, "u_prev overlaps u_cur");
+    }
+    if (step < 0) return fail(SGB_ERR_INVALID_ARG, "step must be >= 0");
+    if (src) {
+        if (!in_inner(g, src->i, src->j, src->k))
+            return fail(SGB_ERR_INVALID_ARG, "source (%d,%d,%d) outside the inner region", src->i,
+                        src->j, src->k);
+        if (!src->wavelet) return fail(SGB_ERR_INVALID_ARG, "source wavelet is NULL");
+    }
+    if ((double)g->dt > cfl_limit(g, g->vmax))
+        return fail(SGB_ERR_UNSTABLE_DT, "dt %g above the CFL limit %g for vmax %g", (double)g->dt,
+                    cfl_limit(g, g->vmax), (double)g->vmax);
+    DevState *ds;
+    if ((rc = device_state(&ds))) return rc;
+    if ((rc = prepare_two_step())) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    StepArgs base;
+    fill_step_constants(g, L, base);
+    base.phi = phi;
+    base.err = ds->err;
+    if (src) {
+        base.si = src->i;
+        base.sj = src->j;
+        base.sk = src->k;
+        base.wavelet = src->wavelet;
+    }
+    PairPlan pp;
+    plan_pair(g, L, *ds, pp);
+    Scratch sc{st, ds->pool, {}};
+    int4 *d_units = nullptr;
+    if (!pp.shell.empty()) {
+        if ((rc = sc.get((void **)&d_units, pp.shell.size() * sizeof(int4)))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(d_units, pp.shell.data(), pp.shell.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, st));
+    }
+    PairMaps pm;
+    if ((rc = encode_pair_maps(pm, u_prev, u_cur, u_next, m, phi ? phi : m, L))) return rc;
+    // the unit table's pageable copy is staged before cudaMemcpyAsync returns;
+    // the scratch is released stream-ordered after the launches
+    return launch_pair(g, pp, pm, d_units, base, u_next, u_next2, u_cur, nullptr, step, st);
+}
 
 extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
                         const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec,
@@ -819,7 +1238,12 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
                                        final_u, d_err);
         break;
     default:
-        rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u, d_err);
+        if (g->time_block == 2)
+            rc = run_shot_pairs(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
+                                final_u, d_err);
+        else
+            rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
+                                   final_u, d_err);
     }
     if (rc) return rc;
     if (host_traces && nt > 0)

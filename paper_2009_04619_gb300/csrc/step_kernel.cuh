@@ -111,6 +111,11 @@ struct StepArgs {
     const float *mu_in;    // MODE_ADJ: mu^{k+1} (padded); phi is mu^k
     int *err;              // device error word
     int tiles_x, tiles_y, zc;
+    // shell launches of a temporally blocked pair: work units (x0, y0, z0, z1)
+    // from a table, and no store inside the box [bx0,bx1) x [by0,by1) x
+    // [bz0,bz1), which the two-step kernel writes
+    const int4 *units;
+    int bx0, bx1, by0, by1, bz0, bz1;
 };
 
 // Counter-based hash (Murmur3 finaliser) of a point index and a step: the random
@@ -329,7 +334,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Per-thread state of one fused-step work unit (a tile x a z-chunk).
-template <class C, class T, int MODE = MODE_FWD>
+template <class C, class T, int MODE = MODE_FWD, bool SHELL = false>
 struct StepCta {
     using E = Elem<T>;
     using G = Stage<C, T, MODE>;
@@ -679,7 +684,11 @@ struct StepCta {
                 f4set(un, e, fmaf(f4get(mm, e), f, f4get(un, e)));
                 if constexpr (MODE == MODE_FWD_ACC) f4set(acc4, e, f4get(acc4, e) + f);
             }
-            if (store_ok && j < a.Ny) {
+            // shell launches leave the box to the two-step kernel (its x bounds
+            // are multiples of 4: a quad is wholly inside or outside)
+            const bool boxed = SHELL && gi >= a.bx0 && gi < a.bx1 && j >= a.by0 && j < a.by1 &&
+                               k >= a.bz0 && k < a.bz1;
+            if (store_ok && j < a.Ny && !boxed) {
                 const long long off = off0 + (long long)r * a.sx;
                 if constexpr (SCALED) {
                     vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(un.x), fabsf(un.y)),
@@ -790,11 +799,11 @@ struct StepMapPtrs {
 // One work unit (tile x z-chunk, index `unit` of `units`) of step n.  With
 // sample_only, only the receivers of the previous step are sampled (the extra
 // launch after a shot's last step).
-template <class C, class T, int MODE = MODE_FWD>
+template <class C, class T, int MODE = MODE_FWD, bool SHELL = false>
 __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &tm, int unit,
                                           int units, int n, bool sample_only)
 {
-    using S = StepCta<C, T, MODE>;
+    using S = StepCta<C, T, MODE, SHELL>;
     using G = Stage<C, T, MODE>;
     static_assert(MODE == MODE_FWD || sizeof(T) == 4, "the adjoint runs in fp32");
     constexpr int TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
@@ -828,14 +837,22 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
 
     // Work unit: chunk-major so that CTAs running together share z and their
     // x-y halos meet in L2.
-    const int per_chunk = a.tiles_x * a.tiles_y;
-    const int chunk = unit / per_chunk;
-    const int trem = unit - chunk * per_chunk;
-    const int tyl = trem / a.tiles_x, txl = trem - tyl * a.tiles_x;
-    st.x0 = txl * BX;
-    st.y0 = tyl * BY;
-    st.z0 = chunk * a.zc;
-    st.z1 = min(st.z0 + a.zc, a.Nz);
+    if constexpr (SHELL) {
+        const int4 u = a.units[unit];
+        st.x0 = u.x;
+        st.y0 = u.y;
+        st.z0 = u.z;
+        st.z1 = u.w;
+    } else {
+        const int per_chunk = a.tiles_x * a.tiles_y;
+        const int chunk = unit / per_chunk;
+        const int trem = unit - chunk * per_chunk;
+        const int tyl = trem / a.tiles_x, txl = trem - tyl * a.tiles_x;
+        st.x0 = txl * BX;
+        st.y0 = tyl * BY;
+        st.z0 = chunk * a.zc;
+        st.z1 = min(st.z0 + a.zc, a.Nz);
+    }
     const int nit = st.z1 - st.z0;
     st.n = n;
     st.aborted = false;
@@ -967,6 +984,21 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     step_unit<C, T>(a, tm, blockIdx.x, gridDim.x, n, false);
+}
+
+// One fused step on the work units of a table, storing nothing inside the
+// two-step kernel's box (the shell of a temporally blocked pair, fp32).
+template <class C>
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+    shell_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tm_ucur,
+                      const __grid_constant__ CUtensorMap tm_ucur_in,
+                      const __grid_constant__ CUtensorMap tm_uprev,
+                      const __grid_constant__ CUtensorMap tm_m,
+                      const __grid_constant__ CUtensorMap tm_phi)
+{
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
+    const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
+    step_unit<C, float, MODE_FWD, true>(a, tm, blockIdx.x, gridDim.x, n, false);
 }
 
 // Forward step that also stores g^n = L u^n + phi^n + f^n (adjoint recomputation).

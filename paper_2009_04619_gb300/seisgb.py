@@ -43,7 +43,8 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("dx", ctypes.c_float), ("dy", ctypes.c_float),
                 ("dz", ctypes.c_float), ("dt", ctypes.c_float), ("vmax", ctypes.c_float),
-                ("pml_r0", ctypes.c_float), ("storage", ctypes.c_int32)]
+                ("pml_r0", ctypes.c_float), ("storage", ctypes.c_int32),
+                ("time_block", ctypes.c_int32)]
 
     @property
     def shape(self):
@@ -105,6 +106,14 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.POINTER(Source), ctypes.POINTER(Receivers),
                                     ctypes.c_void_p]),
+    "stencil_step_scaled": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.POINTER(Source),
+                                           ctypes.POINTER(Receivers), ctypes.c_void_p]),
+    "stencil_step2": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Source),
+                                     ctypes.c_void_p]),
     "run_shot": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -161,9 +170,10 @@ def _check(rc: int):
     return rc
 
 
-def make_grid(nx, ny, nz, nb, dx, dy, dz, dt, vmax, pml_r0=1e-3, storage=FP32) -> Grid:
+def make_grid(nx, ny, nz, nb, dx, dy, dz, dt, vmax, pml_r0=1e-3, storage=FP32,
+              time_block=0) -> Grid:
     return Grid(int(nx), int(ny), int(nz), int(nb), float(dx), float(dy), float(dz), float(dt),
-                float(vmax), float(pml_r0), int(storage))
+                float(vmax), float(pml_r0), int(storage), int(time_block))
 
 
 def layout(g: Grid) -> LayoutInfo:
@@ -230,12 +240,19 @@ def _stream(stream):
     return stream.cuda_stream
 
 
+_WAVE_DTYPE = {FP32: "float32", FP16_SCALED: "float16", BF16: "bfloat16"}
+
+
 def stencil_step(g: Grid, u_cur, u_prev_to_next, m, phi, step: int = 0, source=None,
-                 receivers=None, stream=None):
-    """One fused step.  Fields: CUDA tensors in the padded layout.
+                 receivers=None, stream=None, scale_state=None):
+    """One fused step.  Fields: CUDA tensors in the padded layout; u_cur and
+    u_prev_to_next hold g.storage elements (float32, bfloat16, or float16 for
+    FP16_SCALED, which also needs scale_state: a float32 CUDA tensor of 8 values,
+    see stencil_step_scaled in the C header); m and phi are float32.
     source: (i, j, k, wavelet_cuda_tensor) or None.
     receivers: (ijk int32 numpy [nrec, 3], traces_row cuda tensor [nrec]) or None."""
     E = int(layout(g).elems)
+    wdt = _WAVE_DTYPE.get(int(g.storage), "float32")
     src = None
     if source is not None:
         i, j, k, w = source
@@ -247,13 +264,39 @@ def stencil_step(g: Grid, u_cur, u_prev_to_next, m, phi, step: int = 0, source=N
         keep = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
         rec = Receivers(keep.shape[0], keep.ctypes.data,
                         _buf(row, "traces row", "float32", keep.shape[0], cuda=True))
-    fields = [_buf(f, nm, "float32", E, cuda=True)
-              for f, nm in ((u_cur, "u_cur"), (u_prev_to_next, "u_prev_to_next"), (m, "m"))]
-    rc = lib().stencil_step(ctypes.byref(g), *fields, _buf(phi, "phi", "float32", E, cuda=True),
-                            int(step), ctypes.byref(src) if src is not None else None,
-                            ctypes.byref(rec) if rec is not None else None, _stream(stream))
+    fields = [_buf(u_cur, "u_cur", wdt, E, cuda=True),
+              _buf(u_prev_to_next, "u_prev_to_next", wdt, E, cuda=True),
+              _buf(m, "m", "float32", E, cuda=True)]
+    srcp = ctypes.byref(src) if src is not None else None
+    recp = ctypes.byref(rec) if rec is not None else None
+    php = _buf(phi, "phi", "float32", E, cuda=True)
+    if int(g.storage) == FP16_SCALED:
+        sc = _buf(scale_state, "scale_state", "float32", 8, cuda=True)
+        rc = lib().stencil_step_scaled(ctypes.byref(g), *fields, php, sc, int(step), srcp, recp,
+                                       _stream(stream))
+    else:
+        rc = lib().stencil_step(ctypes.byref(g), *fields, php, int(step), srcp, recp,
+                                _stream(stream))
     del keep
     _check(rc)
+
+
+def stencil_step2(g: Grid, u_prev, u_cur, u_next, u_next2, m, phi, step: int = 0, source=None,
+                  stream=None):
+    """Two steps with temporal blocking on the PML-free interior: reads u^{n-1}
+    (u_prev) and u^n (u_cur), writes u^{n+1} (u_next) and u^{n+2} (u_next2);
+    phi is updated in place.  fp32 CUDA tensors in the padded layout.
+    source: (i, j, k, wavelet_cuda_tensor) or None (samples step and step + 1)."""
+    E = int(layout(g).elems)
+    src = None
+    if source is not None:
+        i, j, k, w = source
+        src = Source(int(i), int(j), int(k), _buf(w, "wavelet", "float32", int(step) + 2, cuda=True))
+    f = [_buf(x, nm, "float32", E, cuda=True) for x, nm in
+         ((u_prev, "u_prev"), (u_cur, "u_cur"), (u_next, "u_next"), (u_next2, "u_next2"),
+          (m, "m"), (phi, "phi"))]
+    _check(lib().stencil_step2(ctypes.byref(g), *f, int(step),
+                               ctypes.byref(src) if src is not None else None, _stream(stream)))
 
 
 def run_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, traces, final_u=None,

@@ -5,6 +5,7 @@ time per launch (CUDA events) -- a small driver for timing and for ncu captures.
     python profile_step.py --adjoint --n 256 --nb 16 --nt 200
     python profile_step.py --storage fp16 --n 512 --nb 32 --nt 40
     python profile_step.py --serve 16
+    python profile_step.py --step2 --n 512 --nb 32 --launches 20
 
 With --adjoint it runs one misfit-gradient shot instead (layered model with a
 Gaussian anomaly, observed traces from the model without it) and reports its
@@ -111,6 +112,47 @@ def _serve(a):
                       "setup_ms": st.setup_ms}))
 
 
+def _step2(a):
+    """Back-to-back pairs of steps: stencil_step2 (four buffers rotating) against
+    two stencil_step launches (in place), CUDA events, same grid and fields."""
+    n_in = a.n - 2 * a.nb
+    h, v = 10.0, 4500.0
+    g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, h, h, h, 1.0, v)
+    dt = 0.4 * seisgb.cfl_dt(g0, v)
+    g = seisgb.make_grid(n_in, n_in, n_in, a.nb, h, h, h, dt, v)
+    L = seisgb.layout(g)
+    f = [torch.zeros(int(L.elems), dtype=torch.float32, device="cuda") for _ in range(6)]
+    vel = torch.full(g.shape, 3000.0, device="cuda")
+    seisgb.pack(g, (vel * dt) ** 2, f[4])
+    w = torch.zeros(2 * (a.warmup + a.launches) + 4, device="cuda")
+    src = (a.n // 2, a.n // 2, a.n // 2)
+    res = {}
+    for mode in ("step2", "step"):
+        def run(k, n):
+            if mode == "step2":
+                p = k % 2  # (f0, f1) -> (f2, f3), then back
+                seisgb.stencil_step2(g, f[2 * p], f[2 * p + 1], f[2 - 2 * p], f[3 - 2 * p], f[4], f[5],
+                                     n, source=(*src, w))
+            else:
+                seisgb.stencil_step(g, f[n % 2], f[(n + 1) % 2], f[4], f[5], n, source=(*src, w))
+                seisgb.stencil_step(g, f[(n + 1) % 2], f[n % 2], f[4], f[5], n + 1, source=(*src, w))
+        for k in range(a.warmup):
+            run(k, 2 * k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(a.launches):
+            run(k, 2 * k)
+        e1.record()
+        torch.cuda.synchronize()
+        seisgb.device_status()
+        res[mode] = e0.elapsed_time(e1) / (2 * a.launches)
+    pts = a.n ** 3
+    print(json.dumps({"n": a.n, "nb": a.nb, "ms_per_step_step2": res["step2"],
+                      "ms_per_step_single": res["step"], "speedup": res["step"] / res["step2"],
+                      "gpts_step2": pts / res["step2"] / 1e6, "gpts_single": pts / res["step"] / 1e6}))
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--n", type=int, default=256, help="computed points per axis")
@@ -125,6 +167,8 @@ def main(argv=None):
                    help="time a short run_shot with 16-bit wavefield storage")
     p.add_argument("--serve", type=int, default=0,
                    help="submit this many requests of the serving mix to a 16-slot server")
+    p.add_argument("--step2", action="store_true",
+                   help="time stencil_step2 (two steps, temporal blocking) against two stencil_step")
     a = p.parse_args(argv)
     if a.lib:
         seisgb.LIB_PATH = a.lib
@@ -138,6 +182,9 @@ def main(argv=None):
         return
     if a.serve:
         _serve(a)
+        return
+    if a.step2:
+        _step2(a)
         return
     n_in = a.n - 2 * a.nb  # nb = 0: no PML, every tile takes the interior path
     h, v = 10.0, 4500.0

@@ -72,7 +72,8 @@ def test_cfl_dt_closed_form(lib):
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("nb", -1), ("dx", 0.0), ("dt", -1.0),
                                          ("pml_r0", 0.0), ("pml_r0", 1.5), ("storage", 7),
-                                         ("vmax", float("nan"))])
+                                         ("vmax", float("nan")), ("time_block", 3),
+                                         ("time_block", -1)])
 def test_bad_grid_rejected_without_gpu(lib, field, value):
     g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
     setattr(g, field, value)
@@ -216,3 +217,31 @@ def test_binding_checks_buffers_before_the_c_call(lib):
         seisgb.stencil_step(g, f, f.copy(), f.copy(), f.copy(), 0)
     with pytest.raises(ValueError, match="CUDA"):
         seisgb.pack(g, v, f)
+
+
+def test_time_block_2_needs_fp32_storage(lib):
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=seisgb.BF16, time_block=2)
+    with pytest.raises(seisgb.SeisgbError) as e:
+        seisgb.layout(g)
+    assert e.value.code == seisgb.ERR_INVALID_ARG and "time_block" in str(e.value)
+
+
+def test_step2_argument_checks_without_gpu(lib):
+    """stencil_step2 validates before any GPU work: four distinct aligned
+    buffers, fp32 storage, phi with a PML, the CFL limit."""
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
+    E = int(seisgb.layout(g).elems)
+    buf = np.zeros(7 * E + 16, np.float32)
+    b = buf.ctypes.data + (16 - buf.ctypes.data % 16) % 16
+    fld = [b + 4 * E * q for q in range(6)]
+    L = seisgb.lib()
+    f = lambda *a: L.stencil_step2(ctypes.byref(g), *a, 0, None, None)
+    assert f(fld[0], fld[1], fld[1], fld[3], fld[4], fld[5]) == seisgb.ERR_INVALID_ARG  # out = in
+    assert "overlaps" in seisgb.last_error()
+    assert f(fld[0], fld[1], fld[2], fld[2], fld[4], fld[5]) == seisgb.ERR_INVALID_ARG  # outs equal
+    assert f(fld[0], fld[1], fld[2], fld[3], fld[4], None) == seisgb.ERR_INVALID_ARG    # no phi
+    assert f(fld[0] + 4, fld[1], fld[2], fld[3], fld[4], fld[5]) == seisgb.ERR_INVALID_ARG
+    g16 = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=seisgb.BF16)
+    assert L.stencil_step2(ctypes.byref(g16), *fld, 0, None, None) == seisgb.ERR_INVALID_ARG
+    g2 = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1.0, 3000)
+    assert L.stencil_step2(ctypes.byref(g2), *fld, 0, None, None) == seisgb.ERR_UNSTABLE_DT

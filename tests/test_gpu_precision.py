@@ -84,3 +84,133 @@ def test_256_cube_1000_steps_error_per_format():
     assert errs["fp32"][0] <= 5e-4 and errs["fp32"][1] <= 5e-4
     assert errs["fp16"][0] <= 5e-2 and errs["fp16"][1] <= 4e-2
     assert errs["bf16"][0] <= 4e-1 and errs["bf16"][1] <= 3e-1
+
+
+# Stored mantissa bits of the 16-bit formats: fp16 keeps 10, bf16 7.
+MANT = {"fp16": 10, "bf16": 7}
+TORCH16 = {"fp16": torch.float16, "bf16": torch.bfloat16}
+
+
+def _padded16(g, stored, fmt):
+    """Padded device field of 16-bit values from compact fp32 values that are
+    already representable in the format (the conversion is exact)."""
+    from gpu_util import to_padded
+    return to_padded(g, stored).to(TORCH16[fmt])
+
+
+def _ulp16(x, p):
+    """Spacing of the 16-bit grid around |x| (normal range)."""
+    ax = np.maximum(np.abs(x), 1e-30)
+    return np.exp2(np.floor(np.log2(ax)) - p)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_stencil_step_16bit_single_step_vs_oracle(fmt):
+    """One step of stencil_step on 16-bit fields from random inputs (ragged grid
+    over several tiles, anisotropic spacing, PML), against oracle.step.  The fp32
+    evaluation has error <= 1e-6 S (S = sum of |terms|, the fp32 bound of the
+    other parity tests); stochastic rounding then picks one of the two 16-bit
+    neighbours of the fp32 value, within one spacing 2^-p |x| of it (p = 10 for
+    fp16, 7 for bf16).  The rounding must also be unbiased: the mean signed error
+    in units of the spacing is ~0."""
+    from gpu_util import abs_term_sum, from_padded, to_padded
+    ensure_lib()
+    nx, ny, nz, nb, h = 90, 37, 29, 5, (10.0, 11.0, 12.0)
+    vmax = 3000.0
+    dt = float(np.float32(0.4 * oracle.cfl_dt(vmax, *h)))
+    storage = FORMATS[fmt]
+    g = seisgb.make_grid(nx, ny, nz, nb, *h, dt, vmax, 1e-3, storage)
+    g32 = seisgb.make_grid(nx, ny, nz, nb, *h, dt, vmax, 1e-3)
+    go = oracle.Grid(nx, ny, nz, nb, *h, dt, vmax=vmax, r0=float(np.float32(1e-3)))
+    rng = np.random.default_rng(16 + len(fmt))
+    sh = g.shape
+    q = lambda a: torch.from_numpy(a.astype(np.float32)).to(TORCH16[fmt]).float().numpy()
+    st_c, st_p = q(rng.standard_normal(sh)), q(rng.standard_normal(sh))
+    s_c, s_p = (2.0 ** -3, 2.0 ** -2) if fmt == "fp16" else (1.0, 1.0)
+    uc, up = st_c * np.float32(s_c), st_p * np.float32(s_p)
+    ph = (0.1 * rng.standard_normal(sh)).astype(np.float32)
+    Nz, Ny, Nx = sh
+    K, J, I = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+    inner = ((I >= nb) & (I < nb + nx) & (J >= nb) & (J < nb + ny) & (K >= nb) & (K < nb + nz))
+    ph[inner] = 0.0
+    vel = rng.uniform(1500, 3000, sh).astype(np.float32)
+    m = (vel.astype(np.float64) ** 2 * dt ** 2).astype(np.float32)
+    src = (nb + nx // 2, nb + ny // 2, nb + nz // 2)
+    wav = np.linspace(-1, 1, 8).astype(np.float32)
+    step = 5
+
+    d_uc, d_up = _padded16(g, st_c, fmt), _padded16(g, st_p, fmt)
+    d_m, d_ph = to_padded(g, m), to_padded(g, ph)
+    d_w = torch.from_numpy(wav).cuda()
+    scale = torch.tensor([1.0] * 4 + [0.0] * 4, dtype=torch.float32, device="cuda")
+    scale[step & 3], scale[(step - 1) & 3] = s_c, s_p
+    scale[4 + (step & 3)] = float(np.abs(uc).max())
+    scale[4 + ((step - 1) & 3)] = float(np.abs(up).max())
+    seisgb.stencil_step(g, d_uc, d_up, d_m, d_ph, step, source=(*src, d_w),
+                        scale_state=scale if fmt == "fp16" else None)
+    seisgb.device_status()
+    s_n = float(scale[(step + 1) & 3]) if fmt == "fp16" else 1.0
+    un = from_padded(g32, d_up.float()) * np.float32(s_n)
+    pn = from_padded(g32, d_ph)
+
+    ref_u, ref_p = oracle.step(go, m, up, uc, ph)
+    inv_vol = 1.0 / (go.dx * go.dy * go.dz)
+    ref_u[src[2], src[1], src[0]] += float(m[src[2], src[1], src[0]]) * float(wav[step]) * inv_vol
+    S = abs_term_sum(go, m, up, uc, ph)
+    S[src[2], src[1], src[0]] += abs(float(m[src[2], src[1], src[0]]) * float(wav[step]) * inv_vol)
+    p = MANT[fmt]
+    err = np.abs(un - ref_u)
+    bound = 1.01e-6 * S + 2.0 ** -p * (np.abs(ref_u) + 1e-6 * S) + 1e-30
+    if fmt == "fp16":
+        bound += 2.0 ** -24 * s_n  # subnormal spacing of the scaled grid
+        assert s_n == 2.0 ** np.round(np.log2(s_n))  # a power of two
+        assert np.abs(un).max() / s_n < 65504.0  # no stored value overflowed
+    assert np.all(err <= bound), float((err / bound).max())
+    # unbiased rounding: mean signed error ~ 0 in units of the 16-bit spacing
+    big = np.abs(ref_u) > 1e3 * 1e-6 * S
+    d = ((un - ref_u) / _ulp16(ref_u, p))[big]
+    assert d.size > 10000 and abs(float(d.mean())) < 0.02, float(d.mean())
+    assert float(np.abs(d).mean()) > 0.2  # the values really were rounded to 16 bits
+    errp = np.abs(pn - ref_p)
+    Sp = np.abs(ph) + np.abs(ref_p) + 1e-6 * S
+    assert np.all(errp <= 1e-6 * Sp + 1e-30), float((errp / Sp).max())
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_run_shot_16bit_equals_stencil_step_loop(fmt):
+    """run_shot with 16-bit storage (CUDA-graph replays) gives bit-identical
+    traces and wavefield to a loop of stencil_step calls on 16-bit fields (the
+    fp16 scale state starting from unit scales and zero maxima)."""
+    from gpu_util import from_padded, to_padded
+    ensure_lib()
+    nx, nb, nt = 20, 6, 70
+    vmax = 2500.0
+    dt = float(np.float32(0.4 * oracle.cfl_dt(vmax, 10.0, 10.0, 10.0)))
+    g = seisgb.make_grid(nx, nx + 3, nx - 2, nb, 10.0, 10.0, 10.0, dt, vmax, 1e-3, FORMATS[fmt])
+    g32 = seisgb.make_grid(nx, nx + 3, nx - 2, nb, 10.0, 10.0, 10.0, dt, vmax)
+    rng = np.random.default_rng(1)
+    vel = rng.uniform(1500, 2500, g.shape).astype(np.float32)
+    wav = synth.ricker(nt, dt, 20.0)
+    src = (nb + 5, nb + 7, nb + 3)
+    rec = np.array([[nb, nb, nb], [nb + 3, nb + 9, nb + 2], [nb + nx - 1, nb + 1, nb + 4]], np.int32)
+    tr = torch.zeros((nt, 3), dtype=torch.float32, device="cuda")
+    u = torch.zeros(g.shape, dtype=torch.float32, device="cuda")
+    d_v, d_w = torch.from_numpy(vel).cuda(), torch.from_numpy(wav).cuda()
+    seisgb.run_shot(g, d_v, d_w, nt, src, rec, tr, u)
+
+    m = (vel * np.float32(dt)) ** 2
+    d_m = to_padded(g32, m)
+    L = seisgb.layout(g)
+    a, b = (torch.zeros(int(L.elems), dtype=TORCH16[fmt], device="cuda") for _ in range(2))
+    ph = torch.zeros(int(L.elems), dtype=torch.float32, device="cuda")
+    scale = torch.tensor([1.0] * 4 + [0.0] * 4, dtype=torch.float32, device="cuda")
+    tr2 = torch.zeros((nt, 3), dtype=torch.float32, device="cuda")
+    cur, prev = a, b
+    for n in range(nt):
+        seisgb.stencil_step(g, cur, prev, d_m, ph, n, source=(*src, d_w), receivers=(rec, tr2[n]),
+                            scale_state=scale if fmt == "fp16" else None)
+        cur, prev = prev, cur
+    s_final = float(scale[nt & 3]) if fmt == "fp16" else 1.0
+    u2 = from_padded(g32, cur.float()) * np.float32(s_final)
+    assert np.array_equal(tr.cpu().numpy(), tr2.cpu().numpy())
+    assert np.array_equal(u.cpu().numpy(), u2)
