@@ -380,12 +380,12 @@ def _stencil_step_ms(g, fmt, seisgb, dev, d_v, dt, src, d_w, launches, nt):
 
 
 def _temporal(a, seisgb, w, vel, vmax, dt, src, rec, d_v, d_w, d_tr, dev, barrier, single, world):
-    """run_shot with time_block 2 on the benchmark workload (CUDA events around
+    """run_shot with SCHED_PAIRS (temporal blocking) on the benchmark workload (CUDA events around
     a.steps shots after one warm-up shot) and the mean time of one
     stencil_step2 pair (back to back)."""
     import torch
     from paper_2009_04619_gb300 import replicas
-    g2 = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, time_block=2)
+    g2 = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, schedule=seisgb.SCHED_PAIRS)
     seisgb.run_shot(g2, d_v, d_w, w.nt, src, rec, d_tr)
     barrier()
     stream = torch.cuda.current_stream()
@@ -419,7 +419,7 @@ def _temporal(a, seisgb, w, vel, vmax, dt, src, rec, d_v, d_w, d_tr, dev, barrie
     del f
     return {"value": val, "unit": UNIT, "ms_per_shot": ms, "vs_single_step": val / single,
             "pair_ms": pair_ms, "ms_per_step_in_pairs": pair_ms / 2,
-            "default": "off (time_block 0); results are bit-identical either way",
+            "default": "off (SCHED_PAIRS is opt-in); results are bit-identical to one step per launch",
             "design": "two-step kernel on the inner region shrunk by 4 points, two single-step "
                       "shell launches on the rest"}
 
@@ -621,7 +621,7 @@ def main():
                          "alg_bytes_per_launch": alg16},
             "error": "relative L2 vs the fp64 oracle: see the 256^3 x 1000-step precision test"}
 
-    # temporal blocking: the same shot with time_block 2 (two steps per HBM
+    # temporal blocking: the same shot with SCHED_PAIRS (two steps per HBM
     # pass on the PML-free interior, identical results), and the pair unit
     temporal = _temporal(a, seisgb, w, vel, vmax, dt, src, rec, d_v, d_w, d_tr, dev, barrier,
                          value, world)

@@ -58,13 +58,25 @@ typedef struct {
     float pml_r0;        /* PML target reflection coefficient in (0, 1];
                             1 switches the damping off */
     int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED or SGB_BF16 */
-    int32_t time_block;  /* run_shot's time steps per pass over HBM: 0 or 1 (one
-                            fused step per launch), or 2 (temporal blocking:
-                            two steps per pass on the PML-free interior, see
-                            stencil_step2; SGB_FP32 storage only).  The result
-                            is the same bits either way.  Other entry points
-                            ignore it. */
+    int32_t schedule;    /* how run_shot launches its time loop (SGB_SCHED_*);
+                            every schedule gives the same bits.  Other entry
+                            points ignore it. */
 } sgb_grid;
+
+/* run_shot time-loop schedules (the arithmetic per point is the same in all):
+ *  SGB_SCHED_AUTO   the library's choice (SGB_SCHED_FLOW, or SGB_SCHED_STEP
+ *                   for SGB_FP16_SCALED storage);
+ *  SGB_SCHED_STEP   one launch per step, replayed in CUDA graphs of 32 steps;
+ *  SGB_SCHED_PAIRS  temporal blocking: two steps per pass over HBM on the
+ *                   PML-free interior, see stencil_step2 (SGB_FP32 only);
+ *  SGB_SCHED_FLOW   one persistent launch for the whole time loop: CTAs take
+ *                   (step, tile) items in order and start an item as soon as
+ *                   its neighbouring tiles have finished the previous step
+ *                   (no per-step tail; SGB_FP32 and SGB_BF16). */
+#define SGB_SCHED_AUTO 0
+#define SGB_SCHED_STEP 1
+#define SGB_SCHED_PAIRS 2
+#define SGB_SCHED_FLOW 3
 
 /* Padded device layout of one field (element counts; multiply by the element
  * size for bytes). */

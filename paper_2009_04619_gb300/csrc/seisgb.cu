@@ -19,6 +19,7 @@
 #include "step_kernel.cuh"
 #include "step_config.cuh"
 #include "two_step.cuh"
+#include "flow_step.cuh"
 
 using namespace sgb;
 
@@ -176,10 +177,12 @@ int check_grid(const sgb_grid *g, sgb_layout_info *L)
         return fail(SGB_ERR_INVALID_ARG, "pml_r0 must be in (0, 1] (got %g)", (double)g->pml_r0);
     if (g->storage != SGB_FP32 && g->storage != SGB_FP16_SCALED && g->storage != SGB_BF16)
         return fail(SGB_ERR_INVALID_ARG, "unknown storage format %d", g->storage);
-    if (g->time_block < 0 || g->time_block > 2)
-        return fail(SGB_ERR_INVALID_ARG, "time_block must be 0, 1 or 2 (got %d)", g->time_block);
-    if (g->time_block == 2 && g->storage != SGB_FP32)
-        return fail(SGB_ERR_INVALID_ARG, "time_block 2 needs SGB_FP32 storage");
+    if (g->schedule < SGB_SCHED_AUTO || g->schedule > SGB_SCHED_FLOW)
+        return fail(SGB_ERR_INVALID_ARG, "unknown schedule %d", g->schedule);
+    if (g->schedule == SGB_SCHED_PAIRS && g->storage != SGB_FP32)
+        return fail(SGB_ERR_INVALID_ARG, "SGB_SCHED_PAIRS needs SGB_FP32 storage");
+    if (g->schedule == SGB_SCHED_FLOW && g->storage == SGB_FP16_SCALED)
+        return fail(SGB_ERR_INVALID_ARG, "SGB_SCHED_FLOW needs SGB_FP32 or SGB_BF16 storage");
     compute_layout(g, L);
     if (L->elems > (int64_t(1) << 40)) return fail(SGB_ERR_INVALID_ARG, "field too large");
     return SGB_OK;
@@ -653,7 +656,7 @@ extern "C" int stencil_step_scaled(const sgb_grid *g, const void *u_cur, void *u
 namespace {
 
 // ---------------------------------------------------------------------------
-// Temporally blocked pairs of steps (time_block 2, stencil_step2)
+// Temporally blocked pairs of steps (SGB_SCHED_PAIRS, stencil_step2)
 // ---------------------------------------------------------------------------
 using TCfg = TwoCfg<56, 16, 8, 8, 6>;
 
@@ -824,13 +827,105 @@ int launch_pair(const sgb_grid *g, const PairPlan &pp, const PairMaps &pm, const
     return SGB_OK;
 }
 
+// The time-loop schedule run_shot uses for grid g.
+int resolve_schedule(const sgb_grid *g)
+{
+    if (g->schedule != SGB_SCHED_AUTO) return g->schedule;
+    return SGB_SCHED_STEP;
+}
+
+// Resident CTAs of the dataflow kernel for storage T (its shared memory and
+// launch bounds are those of the one-step kernel plus two item slots).
+template <class T>
+int prepare_flow(int *occ)
+{
+    const size_t smem = Stage<Cfg, T>::SMEM_BYTES + FLOW_SMEM_EXTRA;
+    CUDA_TRY(cudaFuncSetAttribute(flow_step_kernel<Cfg, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, flow_step_kernel<Cfg, T>, Cfg::BLOCK,
+                                                           smem));
+    if (*occ < 1) return fail(SGB_ERR_CUDA, "dataflow kernel does not fit on an SM");
+    return SGB_OK;
+}
+
+// Steps 0 .. nt-1 of a shot in one persistent dataflow launch.  base: the step
+// constants with phi, error word, source and receivers; maps[p], buf: the
+// tensor maps and buffers of steps of parity p (step n writes buf[n & 1]).
+template <class T>
+int run_flow(const sgb_layout_info &L, DevState *ds, cudaStream_t st, Scratch &sc,
+             const StepArgs &base, const StepMaps (&maps)[2], void *const (&buf)[2], int nt,
+             const int32_t *rec_ijk, int nrec)
+{
+    int rc, occ = 0;
+    if ((rc = prepare_flow<T>(&occ))) return rc;
+    const int ctas = ds->sms * occ;
+    StepArgs fa = base;
+    fa.tiles_x = (L.Nx + Cfg::BX - 1) / Cfg::BX;
+    fa.tiles_y = (L.Ny + Cfg::BY - 1) / Cfg::BY;
+    const int tiles = fa.tiles_x * fa.tiles_y;
+    // z-chunks: the longest (fewest priming planes) that still gives two items
+    // per resident CTA and step; every chunk but the last has >= 8 planes, so a
+    // unit's radius-4 planes lie in its own and the adjacent chunks
+    fa.zc = L.Nz;
+    for (int zc : {32, 24, 16, 12, 8}) {
+        fa.zc = std::min(zc, L.Nz);
+        if ((long long)tiles * ((L.Nz + fa.zc - 1) / fa.zc) >= 2LL * ctas) break;
+    }
+    const int chunks = (L.Nz + fa.zc - 1) / fa.zc, units = tiles * chunks;
+    // receivers grouped by the unit that computes them
+    std::vector<int> rs(units + 1, 0), rl(std::max(nrec, 1));
+    auto unit_of = [&](int r) {
+        const int i = rec_ijk[3 * r], j = rec_ijk[3 * r + 1], k = rec_ijk[3 * r + 2];
+        return (k / fa.zc) * tiles + (j / Cfg::BY) * fa.tiles_x + i / Cfg::BX;
+    };
+    for (int r = 0; r < nrec; ++r) ++rs[unit_of(r) + 1];
+    for (int u = 0; u < units; ++u) rs[u + 1] += rs[u];
+    {
+        std::vector<int> pos(rs.begin(), rs.end() - 1);
+        for (int r = 0; r < nrec; ++r) rl[pos[unit_of(r)]++] = r;
+    }
+    int *d_done, *d_counter, *d_rs, *d_rl;
+    if ((rc = sc.get((void **)&d_done, (size_t)units * 4)) || (rc = sc.get((void **)&d_counter, 16)) ||
+        (rc = sc.get((void **)&d_rs, rs.size() * 4)) || (rc = sc.get((void **)&d_rl, rl.size() * 4)))
+        return rc;
+    CUDA_TRY(cudaMemsetAsync(d_done, 0, (size_t)units * 4, st));
+    CUDA_TRY(cudaMemsetAsync(d_counter, 0, 4, st));
+    CUDA_TRY(cudaMemcpyAsync(d_rs, rs.data(), rs.size() * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_rl, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
+    StepArgs a0 = fa;
+    a0.u_out = nullptr;  // per step: f.buf
+    a0.u_cur = nullptr;
+    a0.step_ptr = nullptr;
+    FlowArgs f;
+    f.buf[0] = buf[0];
+    f.buf[1] = buf[1];
+    f.units = units;
+    f.tiles_x = fa.tiles_x;
+    f.tiles_y = fa.tiles_y;
+    f.n_begin = 0;
+    f.n_end = nt;
+    f.counter = d_counter;
+    f.done = d_done;
+    f.rec_start = d_rs;
+    f.rec_list = d_rl;
+    const StepMaps &p0 = maps[0], &p1 = maps[1];
+    flow_step_kernel<Cfg, T><<<ctas, Cfg::BLOCK, Stage<Cfg, T>::SMEM_BYTES + FLOW_SMEM_EXTRA, st>>>(
+        a0, f, p0.ucur, p0.ucur_in, p0.uprev, p0.m, p0.phi, p1.ucur, p1.ucur_in, p1.uprev,
+        p1.m, p1.phi);
+    CUDA_TRY(cudaGetLastError());
+    ++t_launches;
+    // the pageable copies above are staged before they return; the scratch is
+    // released stream-ordered after the launch
+    return SGB_OK;
+}
+
 // Shot time loop and outputs for wavefield storage T (run_shot after its
 // argument checks and the CFL check).
 template <class T>
 int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
                Scratch &sc, const float *d_vel, const float *d_wav, int nt,
-               const int32_t *src_ijk, int nrec, const long long *d_off, float *d_tr,
-               float *final_u, int *d_err)
+               const int32_t *src_ijk, const int32_t *rec_ijk, int nrec, const long long *d_off,
+               float *d_tr, float *final_u, int *d_err)
 {
     int rc;
     const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
@@ -893,8 +988,15 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         return a;
     };
 
+    bool looped = false;
+    if constexpr (!Elem<T>::SCALED) {
+        if (resolve_schedule(g) == SGB_SCHED_FLOW && nt > 0) {
+            if ((rc = run_flow<T>(L, ds, st, sc, base, maps, buf, nt, rec_ijk, nrec))) return rc;
+            looped = true;
+        }
+    }
     const int GS = 32;  // steps per graph replay (even: the buffer parity repeats)
-    const int replays = nt / GS;
+    const int replays = looped ? 0 : nt / GS;
     if (replays > 0) {
         cudaStream_t cs;
         CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -926,13 +1028,13 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         if (crc) return crc;
         CUDA_TRY(ce);
     }
-    for (int n = replays * GS; n < nt; ++n)
+    for (int n = looped ? nt : replays * GS; n < nt; ++n)
         if ((rc = launch_step<T>(args_for(n, nullptr, n), maps[n & 1], grid, st))) return rc;
 
     // u^{nt}: written by step nt-1 into buf[(nt-1)&1] (u^0 = buf[1] when nt = 0)
     const void *u_final_dev = nt > 0 ? buf[(nt - 1) & 1] : buf[1];
     const float *s_final = ss ? &ss->s[nt & 3] : nullptr;
-    if (nrec > 0 && nt > 0) {
+    if (nrec > 0 && nt > 0 && !looped) {  // the dataflow launch sampled every row itself
         gather_t_kernel<T><<<(nrec + 255) / 256, 256, 0, st>>>(
             static_cast<const T *>(u_final_dev), d_off, nrec, s_final,
             d_tr + (size_t)(nt - 1) * nrec, d_err);
@@ -953,7 +1055,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     return SGB_OK;
 }
 
-// run_shot with time_block 2 (fp32): steps in temporally blocked pairs, an
+// run_shot with SGB_SCHED_PAIRS (fp32): steps in temporally blocked pairs, an
 // odd last step as one ordinary fused step.  Four wavefield buffers: a pair
 // reads (u^{n-1}, u^n) from one two and writes (u^{n+1}, u^{n+2}) to the other.
 int run_shot_pairs(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
@@ -1231,19 +1333,20 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     }
     switch (g->storage) {
     case SGB_FP16_SCALED:
-        rc = run_shot_t<__half>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr, final_u, d_err);
+        rc = run_shot_t<__half>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, rec_ijk, nrec, d_off, d_tr,
+                                final_u, d_err);
         break;
     case SGB_BF16:
-        rc = run_shot_t<__nv_bfloat16>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
-                                       final_u, d_err);
+        rc = run_shot_t<__nv_bfloat16>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, rec_ijk, nrec,
+                                       d_off, d_tr, final_u, d_err);
         break;
     default:
-        if (g->time_block == 2)
+        if (g->schedule == SGB_SCHED_PAIRS)
             rc = run_shot_pairs(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
                                 final_u, d_err);
         else
-            rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
-                                   final_u, d_err);
+            rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, rec_ijk, nrec,
+                                   d_off, d_tr, final_u, d_err);
     }
     if (rc) return rc;
     if (host_traces && nt > 0)

@@ -119,7 +119,11 @@ struct StepArgs {
 };
 
 // Counter-based hash (Murmur3 finaliser) of a point index and a step: the random
-// bits of stochastic rounding, reproducible run to run.
+// bits of stochastic rounding, reproducible run to run.  One hash is drawn per
+// thread and plane; the other 32-bit words that thread needs for the plane come
+// from it by an odd multiply (a bijection of 2^32, so each word is uniform when
+// the hash is, and its low half is a permutation of the hash's low half): see
+// next_bits and Elem<T>::st.
 __device__ __forceinline__ uint32_t hash_bits(uint32_t a, uint32_t b)
 {
     uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u);
@@ -129,6 +133,12 @@ __device__ __forceinline__ uint32_t hash_bits(uint32_t a, uint32_t b)
     h *= 0xC2B2AE35u;
     h ^= h >> 16;
     return h;
+}
+
+// Next random word of the same thread and plane (another row's quad).
+__device__ __forceinline__ uint32_t next_bits(uint32_t h)
+{
+    return (h ^ (h >> 16)) * 0x45D9F3Bu;
 }
 
 // Stochastic rounding of an fp32 pair to 16 bits in the conversion itself
@@ -191,7 +201,8 @@ struct Elem<__half> {
     }
     __device__ static __forceinline__ void st(__half *p, float4 v, uint32_t rnd)
     {
-        __half2 a = pack(v.x, v.y, rnd), b = pack(v.z, v.w, hash_bits(rnd, 0x51u));
+        // the second pair's word: an odd multiple of the first (cheap, uniform)
+        __half2 a = pack(v.x, v.y, rnd), b = pack(v.z, v.w, rnd * 0x9E3779B1u);
         uint2 r;
         r.x = *reinterpret_cast<uint32_t *>(&a);
         r.y = *reinterpret_cast<uint32_t *>(&b);
@@ -227,7 +238,8 @@ struct Elem<__nv_bfloat16> {
     }
     __device__ static __forceinline__ void st(__nv_bfloat16 *p, float4 v, uint32_t rnd)
     {
-        __nv_bfloat162 a = pack(v.x, v.y, rnd), b = pack(v.z, v.w, hash_bits(rnd, 0x51u));
+        // the second pair's word: an odd multiple of the first (cheap, uniform)
+        __nv_bfloat162 a = pack(v.x, v.y, rnd), b = pack(v.z, v.w, rnd * 0x9E3779B1u);
         uint2 r;
         r.x = *reinterpret_cast<uint32_t *>(&a);
         r.y = *reinterpret_cast<uint32_t *>(&b);
@@ -333,9 +345,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Launch variants of the step: one launch per step over the standard units;
+// the shell launches of a temporally blocked pair (units from a table, no store
+// inside the two-step kernel's box); the persistent dataflow launch (CTAs take
+// (step, unit) items in turn, ring slots counted across units).
+enum : int { VAR_PLAIN = 0, VAR_SHELL = 1, VAR_FLOW = 2 };
+
 // Per-thread state of one fused-step work unit (a tile x a z-chunk).
-template <class C, class T, int MODE = MODE_FWD, bool SHELL = false>
+template <class C, class T, int MODE = MODE_FWD, int VAR = VAR_PLAIN>
 struct StepCta {
+    static constexpr bool SHELL = VAR == VAR_SHELL, FLOW = VAR == VAR_FLOW;
     using E = Elem<T>;
     using G = Stage<C, T, MODE>;
     // the adjoint's PML-path band is one point wider: inner points next to the
@@ -359,6 +378,8 @@ struct StepCta {
     int phi_xmask;  // phi blocks holding x-PML columns, when the tile touches only the
                     // x-PML (planes outside the z-PML load only these); 0 otherwise
     int phoff;      // offset of this thread's row-0 quad in the blocked phi tile
+    int useq, pseq;  // FLOW: u and (u^{n-1}, m, phi) planes of earlier units of this CTA
+    void *u_out_v;   // FLOW: the output buffer of the current item's step
     float s_cur, s_prev, inv_s_next;  // fp16 scales (1 otherwise)
     float vmax;                       // running max |u^{n+1}| of this thread
     // PML terms of the thread's fixed columns i = gi + e and rows j = gj0 + r:
@@ -441,7 +462,7 @@ struct StepCta {
 
     __device__ __forceinline__ void issue_u(int p)
     {
-        const int rel = p - z0 + 4;
+        const int rel = p - z0 + 4 + (FLOW ? useq : 0);
         const int s = rel % NU, f = rel / NU;
         if (f > 0) wait(empty_u + s, (f - 1) & 1);  // previous plane of the slot released
         lastf_u[s] = f;
@@ -458,7 +479,7 @@ struct StepCta {
 
     __device__ __forceinline__ void issue_p(int k)
     {
-        const int rel = k - z0;
+        const int rel = k - z0 + (FLOW ? pseq : 0);
         const int s = rel % NP, f = rel / NP;
         if (f > 0) wait(empty_p + s, (f - 1) & 1);
         lastf_p[s] = f;
@@ -492,6 +513,12 @@ struct StepCta {
     // copies to land, so no copy is in flight when it exits.
     __device__ __forceinline__ void produce()
     {
+        produce_unit();
+        drain();
+    }
+
+    __device__ __forceinline__ void produce_unit()
+    {
         int nu = z0 - 4, np = z0;
         while ((nu < z1 + 4 || np < z1) && !aborted) {
             // plane nu is first needed at iteration nu - z0 - 4 (as the front
@@ -501,6 +528,10 @@ struct StepCta {
             else issue_p(np++);
             aborted = *reinterpret_cast<volatile int *>(s_abort) != 0;
         }
+    }
+
+    __device__ __forceinline__ void drain()
+    {
         for (int s = 0; s < NU; ++s)
             if (lastf_u[s] >= 0) mbar_wait_bounded(full_u + s, lastf_u[s] & 1, WAIT_NS);
         for (int s = 0; s < NP; ++s)
@@ -520,14 +551,15 @@ struct StepCta {
         constexpr bool ZP = KIND == PLANE_Z;
         const StepArgs &a = *pa;
         const int k = z0 + it;
-        const int relf = it + 8;
+        const int relf = it + 8 + (FLOW ? useq : 0);
         const int sf = relf % NU;
         wait(full_u + sf, (relf / NU) & 1);
 #pragma unroll
         for (int r = 0; r < TY; ++r) q[r][O + 8] = E::ld(ustage(sf) + own_off(k + 4, r));
-        const int sq = it % NP;
-        wait(full_p + sq, (it / NP) & 1);
-        const int sc = (it + 4) % NU;
+        const int itp = it + (FLOW ? pseq : 0);
+        const int sq = itp % NP;
+        wait(full_p + sq, (itp / NP) & 1);
+        const int sc = (it + 4 + (FLOW ? useq : 0)) % NU;
         const T *cu = ustage(sc);
         const unsigned char *pu = sp + sq * G::P_BYTES;
         const T *pup = reinterpret_cast<const T *>(pu);
@@ -566,6 +598,9 @@ struct StepCta {
         bool zin = false;
         if (PML) pml_axis(a.nz, k, a.az, a.kz, ez, gzk, hzp, hzm, zin);
         const long long off0 = base_off + (long long)k * a.sxy;
+        // random bits of this thread's stores in this plane (16-bit storage)
+        uint32_t rnd = 0;
+        if constexpr (sizeof(T) == 2) rnd = hash_bits((uint32_t)off0, (uint32_t)n);
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
             const T *rowp = cu + (row0 + r) * SW + colu;
@@ -695,9 +730,7 @@ struct StepCta {
                                              fmaxf(fabsf(un.z), fabsf(un.w))));
                     un = f4mul(inv_s_next, un);
                 }
-                T *uo = static_cast<T *>(a.u_out) + off;
-                uint32_t rnd = 0;
-                if constexpr (sizeof(T) == 2) rnd = hash_bits((uint32_t)off, (uint32_t)n);
+                T *uo = static_cast<T *>(FLOW ? u_out_v : a.u_out) + off;
                 const bool wphi = PML && any_pml;  // phi^{n+1}, or mu^k in the adjoint
                 if (gi + 3 < a.Nx) {
                     E::st(uo, un, rnd);
@@ -710,6 +743,7 @@ struct StepCta {
                         if constexpr (MODE == MODE_FWD_ACC) a.acc_out[off + e] = f4get(acc4, e);
                     }
                 }
+                if constexpr (sizeof(T) == 2) rnd = next_bits(rnd);  // the next row's word
                 if constexpr (MODE == MODE_ADJ) {
                     // S += w^k g^{k-1} (dJ/dm = sum_k w^k g^{k-1} / m; S is folded
                     // into the fp64 sum every few steps)
@@ -732,6 +766,76 @@ struct StepCta {
             mbar_arrive(empty_p + sq);
         }
         aborted = *reinterpret_cast<volatile int *>(s_abort) != 0;
+    }
+
+    // Tile-level geometry of the unit (x0, y0, z0, z1 set): whether the tile
+    // touches the x-y PML band, and which phi blocks its planes need.
+    __device__ __forceinline__ void unit_geometry()
+    {
+        const StepArgs &a = *pa;
+        const int xe = min(x0 + BX, a.Nx), ye = min(y0 + BY, a.Ny);
+        xy_inner = x0 >= a.nb + BAND && xe <= a.nb + a.nx - BAND && y0 >= a.nb + BAND &&
+                   ye <= a.nb + a.ny - BAND;
+        phi_xmask = 0;
+        if (MODE != MODE_ADJ && !xy_inner && y0 >= a.nb && ye <= a.nb + a.ny) {
+            // rows all y-inner: only columns in the x-PML need phi outside the z-PML
+            for (int b = 0; b < C::PHI_NB; ++b) {
+                const int c0 = x0 + b * C::PHI_BW, c1 = min(c0 + C::PHI_BW, a.Nx);
+                if (c0 < a.Nx && (c0 < a.nb || c1 > a.nb + a.nx)) phi_xmask |= 1 << b;
+            }
+        }
+    }
+
+    // This consumer thread's points in the unit and their PML tables.
+    __device__ __forceinline__ void thread_geometry()
+    {
+        const StepArgs &a = *pa;
+        const int txi = tid % C::TXT, tyi = tid / C::TXT;
+        row0 = R + TY * tyi;
+        colu = G::HX + 4 * txi;
+        gi = x0 + 4 * txi;
+        gj0 = y0 + TY * tyi;
+        prow = (TY * tyi) * BX + 4 * txi;
+        phoff = (4 * txi / C::PHI_BW) * C::PHI_BW * BY + (TY * tyi) * C::PHI_BW + (4 * txi) % C::PHI_BW;
+        store_ok = gi < a.Nx;
+        base_off = a.origin + (long long)gj0 * a.sx + gi;
+        pml_tables();
+    }
+
+    // Prime the register queue with planes z0-4 .. z0+3 and run the unit's
+    // planes: z-PML planes below the inner region, then the planes outside the
+    // z-PML (interior path, or the PML path for tiles touching the x-y PML band
+    // and for the adjoint's band planes next to the z-PML), then the z-PML
+    // planes above it.
+    __device__ __forceinline__ void consume_unit(float4 (&q)[TY][QN])
+    {
+        const StepArgs &a = *pa;
+        const int nit = z1 - z0;
+        const int u0 = FLOW ? useq : 0;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            wait(full_u + (u0 + s) % NU, ((u0 + s) / NU) & 1);
+#pragma unroll
+            for (int r = 0; r < TY; ++r) q[r][s] = E::ld(ustage((u0 + s) % NU) + own_off(z0 - 4 + s, r));
+        }
+        // planes z0-4 .. z0-1 are not needed again
+        __syncwarp();
+        if (lane == 0)
+            for (int s = 0; s < 4; ++s) mbar_arrive(empty_u + (u0 + s) % NU);
+        aborted = *reinterpret_cast<volatile int *>(s_abort) != 0;
+        const int zlo = min(max(a.nb - z0, 0), nit);
+        const int zhi = min(max(a.nb + a.nz - z0, zlo), nit);
+        segment<PLANE_Z>(q, 0, zlo);
+        if (!xy_inner) {
+            segment<PLANE_XY>(q, zlo, zhi);
+        } else {
+            const int b0 = min(max(a.nb + BAND - z0, zlo), zhi);
+            const int b1 = min(max(a.nb + a.nz - BAND - z0, b0), zhi);
+            segment<PLANE_XY>(q, zlo, b0);
+            segment<PLANE_INTERIOR>(q, b0, b1);
+            segment<PLANE_XY>(q, b1, zhi);
+        }
+        segment<PLANE_Z>(q, zhi, nit);
     }
 
     template <int O>
@@ -799,11 +903,12 @@ struct StepMapPtrs {
 // One work unit (tile x z-chunk, index `unit` of `units`) of step n.  With
 // sample_only, only the receivers of the previous step are sampled (the extra
 // launch after a shot's last step).
-template <class C, class T, int MODE = MODE_FWD, bool SHELL = false>
+template <class C, class T, int MODE = MODE_FWD, int VAR = VAR_PLAIN>
 __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &tm, int unit,
                                           int units, int n, bool sample_only)
 {
-    using S = StepCta<C, T, MODE, SHELL>;
+    using S = StepCta<C, T, MODE, VAR>;
+    constexpr bool SHELL = VAR == VAR_SHELL;
     using G = Stage<C, T, MODE>;
     static_assert(MODE == MODE_FWD || sizeof(T) == 4, "the adjoint runs in fp32");
     constexpr int TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
@@ -884,17 +989,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
 
     if (sample_only) return;
 
-    const int xe = min(st.x0 + BX, a.Nx), ye = min(st.y0 + BY, a.Ny);
-    st.xy_inner = st.x0 >= a.nb + S::BAND && xe <= a.nb + a.nx - S::BAND &&
-                  st.y0 >= a.nb + S::BAND && ye <= a.nb + a.ny - S::BAND;
-    st.phi_xmask = 0;
-    if (MODE != MODE_ADJ && !st.xy_inner && st.y0 >= a.nb && ye <= a.nb + a.ny) {
-        // rows all y-inner: only columns in the x-PML need phi outside the z-PML
-        for (int b = 0; b < C::PHI_NB; ++b) {
-            const int c0 = st.x0 + b * C::PHI_BW, c1 = min(c0 + C::PHI_BW, a.Nx);
-            if (c0 < a.Nx && (c0 < a.nb || c1 > a.nb + a.nx)) st.phi_xmask |= 1 << b;
-        }
-    }
+    st.unit_geometry();
 
     if (tid == THREADS) {
         *st.s_abort = 0;
@@ -918,50 +1013,9 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
         return;
     }
 
-    const int txi = tid % C::TXT, tyi = tid / C::TXT;
-    st.row0 = R + TY * tyi;
-    st.colu = G::HX + 4 * txi;
-    st.gi = st.x0 + 4 * txi;
-    st.gj0 = st.y0 + TY * tyi;
-    st.prow = (TY * tyi) * BX + 4 * txi;
-    st.phoff = (4 * txi / C::PHI_BW) * C::PHI_BW * BY + (TY * tyi) * C::PHI_BW + (4 * txi) % C::PHI_BW;
-    st.store_ok = st.gi < a.Nx;
-    st.base_off = a.origin + (long long)st.gj0 * a.sx + st.gi;
-    st.pml_tables();
-
-    // Prime the register queue with planes z0-4 .. z0+3 (first fill of slots 0..7).
+    st.thread_geometry();
     float4 q[TY][C::QN];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        st.wait(st.full_u + s, 0);
-#pragma unroll
-        for (int r = 0; r < TY; ++r) q[r][s] = Elem<T>::ld(st.ustage(s) + st.own_off(st.z0 - 4 + s, r));
-    }
-    // planes z0-4 .. z0-1 (slots 0..3) are not needed again
-    __syncwarp();
-    if (st.lane == 0)
-        for (int s = 0; s < 4; ++s) mbar_arrive(st.empty_u + s);
-    st.aborted = *reinterpret_cast<volatile int *>(st.s_abort) != 0;
-
-    // z segments: z-PML planes below the inner region, then the planes
-    // outside the z-PML (interior path, or the PML path for tiles touching the
-    // x-y PML band and for the adjoint's band planes next to the z-PML), then
-    // the z-PML planes above it.
-    {
-        const int zlo = min(max(a.nb - st.z0, 0), nit);
-        const int zhi = min(max(a.nb + a.nz - st.z0, zlo), nit);
-        st.template segment<PLANE_Z>(q, 0, zlo);
-        if (!st.xy_inner) {
-            st.template segment<PLANE_XY>(q, zlo, zhi);
-        } else {
-            const int b0 = min(max(a.nb + S::BAND - st.z0, zlo), zhi);
-            const int b1 = min(max(a.nb + a.nz - S::BAND - st.z0, b0), zhi);
-            st.template segment<PLANE_XY>(q, zlo, b0);
-            st.template segment<PLANE_INTERIOR>(q, b0, b1);
-            st.template segment<PLANE_XY>(q, b1, zhi);
-        }
-        st.template segment<PLANE_Z>(q, zhi, nit);
-    }
+    st.consume_unit(q);
 
     if constexpr (S::SCALED) {  // max |u^{n+1}| for the next step's scale
         float v = st.vmax;
@@ -998,7 +1052,7 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
 {
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
-    step_unit<C, float, MODE_FWD, true>(a, tm, blockIdx.x, gridDim.x, n, false);
+    step_unit<C, float, MODE_FWD, VAR_SHELL>(a, tm, blockIdx.x, gridDim.x, n, false);
 }
 
 // Forward step that also stores g^n = L u^n + phi^n + f^n (adjoint recomputation).

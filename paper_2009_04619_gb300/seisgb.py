@@ -30,6 +30,12 @@ FP32 = 0
 FP16_SCALED = 1
 BF16 = 2
 
+# run_shot time-loop schedules (sgb_grid.schedule)
+SCHED_AUTO = 0
+SCHED_STEP = 1
+SCHED_PAIRS = 2
+SCHED_FLOW = 3
+
 
 class SeisgbError(RuntimeError):
     def __init__(self, code: int, msg: str):
@@ -44,7 +50,7 @@ class Grid(ctypes.Structure):
                 ("nb", ctypes.c_int32), ("dx", ctypes.c_float), ("dy", ctypes.c_float),
                 ("dz", ctypes.c_float), ("dt", ctypes.c_float), ("vmax", ctypes.c_float),
                 ("pml_r0", ctypes.c_float), ("storage", ctypes.c_int32),
-                ("time_block", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32)]
 
     @property
     def shape(self):
@@ -171,9 +177,9 @@ def _check(rc: int):
 
 
 def make_grid(nx, ny, nz, nb, dx, dy, dz, dt, vmax, pml_r0=1e-3, storage=FP32,
-              time_block=0) -> Grid:
+              schedule=0) -> Grid:
     return Grid(int(nx), int(ny), int(nz), int(nb), float(dx), float(dy), float(dz), float(dt),
-                float(vmax), float(pml_r0), int(storage), int(time_block))
+                float(vmax), float(pml_r0), int(storage), int(schedule))
 
 
 def layout(g: Grid) -> LayoutInfo:

@@ -6,6 +6,7 @@ time per launch (CUDA events) -- a small driver for timing and for ncu captures.
     python profile_step.py --storage fp16 --n 512 --nb 32 --nt 40
     python profile_step.py --serve 16
     python profile_step.py --step2 --n 512 --nb 32 --launches 20
+    python profile_step.py --shots --n 256 --nb 16 --nt 200 --launches 3
 
 With --adjoint it runs one misfit-gradient shot instead (layered model with a
 Gaussian anomaly, observed traces from the model without it) and reports its
@@ -112,6 +113,44 @@ def _serve(a):
                       "setup_ms": st.setup_ms}))
 
 
+def _shots(a):
+    """run_shot on an n^3 grid (PML nb, layered model, surface receivers every
+    4th point, nt steps, device-resident inputs) with each time-loop schedule:
+    ms per step (CUDA events around `launches` shots after a warm-up shot)."""
+    n_in = a.n - 2 * a.nb
+    shape = (a.n, a.n, a.n)
+    vel = torch.from_numpy(synth.layered_model(shape, seed=2009)).cuda()
+    vmax = float(vel.max())
+    g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, 1.0, vmax)
+    dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, vmax)))
+    wav = torch.from_numpy(synth.ricker(a.nt, dt, 10.0)).cuda()
+    rec = synth.surface_receivers(n_in, n_in, a.nb, 4)
+    tr = torch.zeros((a.nt, rec.shape[0]), device="cuda")
+    src = (a.n // 2, a.n // 2, a.nb + 2)
+    out = {"n": a.n, "nb": a.nb, "nt": a.nt}
+    scheds = {"step": seisgb.SCHED_STEP, "flow": seisgb.SCHED_FLOW}
+    if a.storage:
+        fmt = {"fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
+    else:
+        fmt = seisgb.FP32
+    for name, sched in scheds.items():
+        if fmt == seisgb.FP16_SCALED and sched == seisgb.SCHED_FLOW:
+            continue
+        g = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, dt, vmax, storage=fmt,
+                             schedule=sched)
+        seisgb.run_shot(g, vel, wav, a.nt, src, rec, tr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.launches):
+            seisgb.run_shot(g, vel, wav, a.nt, src, rec, tr)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.launches / a.nt
+        out[name] = {"ms_per_step": ms, "gpts": a.n ** 3 / ms / 1e6}
+    print(json.dumps(out))
+
+
 def _step2(a):
     """Back-to-back pairs of steps: stencil_step2 (four buffers rotating) against
     two stencil_step launches (in place), CUDA events, same grid and fields."""
@@ -167,6 +206,8 @@ def main(argv=None):
                    help="time a short run_shot with 16-bit wavefield storage")
     p.add_argument("--serve", type=int, default=0,
                    help="submit this many requests of the serving mix to a 16-slot server")
+    p.add_argument("--shots", action="store_true",
+                   help="time whole run_shot calls (layered model) with each time-loop schedule")
     p.add_argument("--step2", action="store_true",
                    help="time stencil_step2 (two steps, temporal blocking) against two stencil_step")
     a = p.parse_args(argv)
@@ -185,6 +226,9 @@ def main(argv=None):
         return
     if a.step2:
         _step2(a)
+        return
+    if a.shots:
+        _shots(a)
         return
     n_in = a.n - 2 * a.nb  # nb = 0: no PML, every tile takes the interior path
     h, v = 10.0, 4500.0

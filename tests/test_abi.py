@@ -72,8 +72,8 @@ def test_cfl_dt_closed_form(lib):
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("nb", -1), ("dx", 0.0), ("dt", -1.0),
                                          ("pml_r0", 0.0), ("pml_r0", 1.5), ("storage", 7),
-                                         ("vmax", float("nan")), ("time_block", 3),
-                                         ("time_block", -1)])
+                                         ("vmax", float("nan")), ("schedule", 4),
+                                         ("schedule", -1)])
 def test_bad_grid_rejected_without_gpu(lib, field, value):
     g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
     setattr(g, field, value)
@@ -219,11 +219,18 @@ def test_binding_checks_buffers_before_the_c_call(lib):
         seisgb.pack(g, v, f)
 
 
-def test_time_block_2_needs_fp32_storage(lib):
-    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=seisgb.BF16, time_block=2)
-    with pytest.raises(seisgb.SeisgbError) as e:
-        seisgb.layout(g)
-    assert e.value.code == seisgb.ERR_INVALID_ARG and "time_block" in str(e.value)
+def test_schedules_check_storage(lib):
+    """Temporal blocking needs fp32 fields; the dataflow schedule has no per-step
+    fp16 scale (fp32 and bf16 only)."""
+    for storage, sched in ((seisgb.BF16, seisgb.SCHED_PAIRS), (seisgb.FP16_SCALED, seisgb.SCHED_PAIRS),
+                           (seisgb.FP16_SCALED, seisgb.SCHED_FLOW)):
+        g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=storage, schedule=sched)
+        with pytest.raises(seisgb.SeisgbError) as e:
+            seisgb.layout(g)
+        assert e.value.code == seisgb.ERR_INVALID_ARG and "SCHED" in str(e.value)
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=seisgb.BF16,
+                         schedule=seisgb.SCHED_FLOW)
+    seisgb.layout(g)
 
 
 def test_step2_argument_checks_without_gpu(lib):

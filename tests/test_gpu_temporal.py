@@ -1,10 +1,10 @@
 """Temporal blocking (two time steps per HBM pass on the PML-free interior):
-stencil_step2 and run_shot with time_block 2 against single steps and the fp64
+stencil_step2 and run_shot with SCHED_PAIRS against single steps and the fp64
 oracle.
 
 The two-step kernel evaluates the interior path's arithmetic operation for
 operation, and the shell launches are the single-step kernel itself, so the
-results must equal two stencil_step calls (and time_block 0) bit for bit.  Each
+results must equal two stencil_step calls (and SCHED_STEP) bit for bit.  Each
 of the two steps is also checked against oracle.step at the per-point bound of
 the single-step parity tests (1e-6 S)."""
 import numpy as np
@@ -32,9 +32,9 @@ def _lib():
     ensure_lib()
 
 
-def _grid_pair(nx, ny, nz, nb, h, vmax=3000.0, time_block=0):
+def _grid_pair(nx, ny, nz, nb, h, vmax=3000.0, schedule=1):
     dt = float(np.float32(0.4 * oracle.cfl_dt(vmax, *h)))
-    g = seisgb.make_grid(nx, ny, nz, nb, *h, dt, vmax, 1e-3, time_block=time_block)
+    g = seisgb.make_grid(nx, ny, nz, nb, *h, dt, vmax, 1e-3, schedule=schedule)
     go = oracle.Grid(nx, ny, nz, nb, float(np.float32(h[0])), float(np.float32(h[1])),
                      float(np.float32(h[2])), dt, vmax=float(np.float32(vmax)),
                      r0=float(np.float32(1e-3)))
@@ -116,9 +116,9 @@ def _shot(g, vel, wav, nt, src, rec):
 
 
 @pytest.mark.parametrize("nt", [100, 71])
-def test_run_shot_time_block_2_small_case(nt):
-    """The small forward-modelling case (64^3 + PML 16) with time_block 2: the
-    same bits as time_block 0 (graph replays of 16 pairs, direct pairs, an odd
+def test_run_shot_pairs_small_case(nt):
+    """The small forward-modelling case (64^3 + PML 16) with SCHED_PAIRS: the
+    same bits as SCHED_STEP (graph replays of 16 pairs, direct pairs, an odd
     last step), and within 2e-5 relative L2 of the fp64 oracle."""
     w = synth.SMALL
     vmax = w.v_const
@@ -129,18 +129,18 @@ def test_run_shot_time_block_2_small_case(nt):
     rec = synth.surface_receivers(w.nx, w.ny, w.nb, 4)
     rec[::2, 2] = src[2]  # half on the source plane: they record the direct wave
     res = {}
-    for tb in (0, 2):
-        g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, time_block=tb)
+    for tb in (seisgb.SCHED_STEP, seisgb.SCHED_PAIRS):
+        g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, schedule=tb)
         res[tb] = _shot(g, vel, wav, nt, src, rec)
-    assert np.array_equal(res[0][0], res[2][0]) and np.array_equal(res[0][1], res[2][1])
+    assert np.array_equal(res[seisgb.SCHED_STEP][0], res[seisgb.SCHED_PAIRS][0]) and np.array_equal(res[seisgb.SCHED_STEP][1], res[seisgb.SCHED_PAIRS][1])
     go = oracle.Grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax=vmax, r0=float(np.float32(1e-3)))
     ref = oracle.run_shot(go, vel, wav, nt, src, rec)
-    assert rel_l2(res[2][1], ref["u"]) <= 2e-5 and rel_l2(res[2][0], ref["traces"]) <= 2e-5
+    assert rel_l2(res[seisgb.SCHED_PAIRS][1], ref["u"]) <= 2e-5 and rel_l2(res[seisgb.SCHED_PAIRS][0], ref["traces"]) <= 2e-5
 
 
-def test_run_shot_time_block_2_layered_ragged():
+def test_run_shot_pairs_layered_ragged():
     """A ragged anisotropic layered grid, source near a corner of the inner
-    region (in the band the shell launches compute): same bits as time_block 0."""
+    region (in the band the shell launches compute): same bits as SCHED_STEP."""
     nx, ny, nz, nb, nt = 101, 45, 38, 7, 67
     shape = (nz + 2 * nb, ny + 2 * nb, nx + 2 * nb)
     vel = synth.layered_model(shape, seed=21, sigma=2.0)
@@ -151,19 +151,19 @@ def test_run_shot_time_block_2_layered_ragged():
     src = (nb + 1, nb + 2, nb + 2)
     rec = synth.surface_receivers(nx, ny, nb, 5)
     res = {}
-    for tb in (0, 2):
-        g = seisgb.make_grid(nx, ny, nz, nb, *h, dt, vmax, time_block=tb)
+    for tb in (seisgb.SCHED_STEP, seisgb.SCHED_PAIRS):
+        g = seisgb.make_grid(nx, ny, nz, nb, *h, dt, vmax, schedule=tb)
         res[tb] = _shot(g, vel, wav, nt, src, rec)
-    assert np.abs(res[0][0]).max() > 0
-    assert np.array_equal(res[0][0], res[2][0]) and np.array_equal(res[0][1], res[2][1])
+    assert np.abs(res[seisgb.SCHED_STEP][0]).max() > 0
+    assert np.array_equal(res[seisgb.SCHED_STEP][0], res[seisgb.SCHED_PAIRS][0]) and np.array_equal(res[seisgb.SCHED_STEP][1], res[seisgb.SCHED_PAIRS][1])
 
 
 @pytest.mark.slow
-def test_run_shot_time_block_2_full_size():
+def test_run_shot_pairs_full_size():
     """The 512^3 benchmark grid (448^3 inner + 32-point PML, layered model) in
     the launch configuration the benchmark times, 40 steps (one graph replay of
     16 pairs, then 4 direct pairs): traces and final wavefield bit-identical to
-    time_block 0 (compared on the device)."""
+    SCHED_STEP (compared on the device)."""
     w = synth.LARGE
     vel = w.velocity()
     vmax = float(vel.max())
@@ -173,11 +173,11 @@ def test_run_shot_time_block_2_full_size():
     rec = w.receivers()
     d_v, d_w = torch.from_numpy(vel).cuda(), torch.from_numpy(wav).cuda()
     out = {}
-    for tb in (0, 2):
-        g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, time_block=tb)
+    for tb in (seisgb.SCHED_STEP, seisgb.SCHED_PAIRS):
+        g = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, schedule=tb)
         tr = torch.zeros((nt, rec.shape[0]), dtype=torch.float32, device="cuda")
         u = torch.zeros(g.shape, dtype=torch.float32, device="cuda")
         seisgb.run_shot(g, d_v, d_w, nt, w.source(), rec, tr, u)
         out[tb] = (tr, u)
-    assert float(out[0][1].abs().max()) > 0
-    assert torch.equal(out[0][0], out[2][0]) and torch.equal(out[0][1], out[2][1])
+    assert float(out[seisgb.SCHED_STEP][1].abs().max()) > 0
+    assert torch.equal(out[seisgb.SCHED_STEP][0], out[seisgb.SCHED_PAIRS][0]) and torch.equal(out[seisgb.SCHED_STEP][1], out[seisgb.SCHED_PAIRS][1])
