@@ -242,10 +242,11 @@ int run_shot_noalloc(const sgb_grid *g, const float *velocity, const float *wave
  * current device at serve_create), a stream and a scheduler thread.  Requests
  * are admitted in FIFO order whenever a slot is free and the server's HBM
  * budget can hold their footprint; all resident shots, whatever their grid
- * sizes, advance together: each time step is one launch that covers the work
- * units of every resident shot, and steps run in CUDA graphs of
- * steps_per_graph launches.  Shots join and leave between graph replays.  A
- * shot's results equal run_shot's for the same request.
+ * sizes, advance together in replays of one CUDA graph that holds, for every
+ * resident shot, a branch of steps_per_graph fused-step launches on that shot's
+ * own grid; the branches run concurrently on the GPU.  Shots join and leave
+ * between graph replays.  A shot's results equal run_shot's for the same
+ * request, bit for bit.
  * ------------------------------------------------------------------------- */
 typedef struct {
     uint64_t hbm_budget_bytes;  /* device memory the resident shots may hold */

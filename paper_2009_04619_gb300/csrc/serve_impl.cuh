@@ -7,23 +7,27 @@
 // - serve_submit deep-copies the request, checks it (arguments, CFL of the
 //   model's maximum velocity, footprint vs. the whole budget) and queues it.
 // - The scheduler thread admits queued requests in FIFO order while a slot is
-//   free and the budget holds the head's footprint, sets their fields up on
-//   the server's stream, and advances every resident shot with graph replays
-//   of steps_per_graph launches of multi_step_kernel.  One launch = one time
-//   step of every resident shot: its grid is the concatenation of all shots'
-//   work units; each CTA finds its shot in a device table (step arguments +
-//   tensor maps per shot) and runs the same per-unit step code as
-//   fused_step_kernel.  Shots with different grid sizes share a launch.
-// - A shot of nt steps takes nt + 1 launches: the extra one samples the
-//   receivers of the last step.  Launches past that idle for the shot.
+//   free and the budget holds the head's footprint, sets their fields up on a
+//   second stream while the current replays run, and advances every resident
+//   shot with replays of one CUDA graph.  The graph has one branch per resident
+//   shot: steps_per_graph launches of the fused step on that shot's own grid
+//   and decomposition (arguments and tensor maps in the kernel's parameter
+//   space, as in run_shot), then an increment of the shot's device step
+//   counter.  The branches are independent, so the shots' kernels run
+//   concurrently and fill each other's partial waves; shots of different grid
+//   sizes share the GPU.
+// - Each launch reads its step from the shot's counter and chooses the
+//   buffers and tensor maps of that step's parity, so a replay of any length
+//   repeats.  A shot of nt steps takes nt + 1 launches (the last samples the
+//   receivers of the last step); launches past that return at once.
 // - Composition changes (admission, retirement) happen between replays; the
 //   graph is re-captured only then.  Retired shots' traces are copied to the
 //   host and their device memory returned to the pool.
-// - Each replay ends by bumping a device replay counter, so the host enqueues
-//   several replays back to back and waits only where the composition can
-//   change: up to the next shot completion when no request can be admitted
-//   (slots full), at most MAX_AHEAD_OPEN replays while slots are free (new
-//   arrivals wait at most that long), one replay while an admission is set up.
+// - The host enqueues several replays back to back and waits only where the
+//   composition can change: up to the next shot completion when no request can
+//   be admitted (slots full), at most MAX_AHEAD_OPEN replays while slots are
+//   free (new arrivals wait at most that long), one replay while an admission
+//   is set up.
 #pragma once
 #include <chrono>
 #include <condition_variable>
@@ -36,49 +40,6 @@ namespace {
 constexpr int SERVE_MAX_SLOTS = 64;
 constexpr int MAX_AHEAD_OPEN = 4;     // replays enqueued at once while slots are free
 constexpr int MAX_AHEAD_FULL = 256;   // ... while every slot is taken
-
-// One resident shot as the multi-shot kernel sees it.
-struct alignas(128) ShotEntry {
-    CUtensorMap maps[2][5];  // [parity of n][u^n halo, u^n interior, u^{n-1}, m, phi]
-    StepArgs args[2];        // [parity of n]: output and current buffers swap each step
-    int unit_begin, units, nt, n0;  // n0: step of the replay's first launch
-};
-
-__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
-{
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                     reinterpret_cast<uint64_t>(m))
-                 : "memory");
-}
-
-// Launch i of replay r (r = *replays, counted since the table was uploaded):
-// step n0 + r * steps_per_graph + i of every resident shot.
-__global__ void __launch_bounds__(Cfg::BLOCK, Cfg::MINB)
-    multi_step_kernel(const ShotEntry *__restrict__ table, int nshots, int launch_i,
-                      const int *__restrict__ replays, int steps_per_graph)
-{
-    // The CTA's shot: the number of shots whose first unit is <= blockIdx.x,
-    // minus one.  Each warp reads the start units in parallel (one lane per
-    // shot) instead of walking the table one dependent load at a time (no
-    // shared memory: the step's TMA destinations start at the dynamic base).
-    const int b = blockIdx.x;
-    const int lane = threadIdx.x & 31;
-    int count = 0;
-    for (int base = 0; base < nshots; base += 32) {
-        const int q = base + lane;
-        const bool le = q < nshots && table[q].unit_begin <= b;
-        count += __popc(__ballot_sync(0xffffffffu, le));
-    }
-    const ShotEntry &e = table[count - 1];
-    const int n = e.n0 + *replays * steps_per_graph + launch_i;
-    if (n > e.nt) return;  // finished: waits for retirement
-    const CUtensorMap *mp = e.maps[n & 1];
-    if (threadIdx.x == Cfg::THREADS)  // the producer lane reads the descriptors
-        for (int q = 0; q < 5; ++q) tensormap_acquire(mp + q);
-    __syncthreads();
-    const StepMapPtrs tm = {mp, mp + 1, mp + 2, mp + 3, mp + 4};
-    step_unit<Cfg, float>(e.args[n & 1], tm, b - e.unit_begin, e.units, n, n == e.nt);
-}
 
 using Clock = std::chrono::steady_clock;
 
@@ -101,9 +62,12 @@ struct Shot {
     float *u0 = nullptr, *u1 = nullptr, *phi = nullptr, *m = nullptr, *d_vel = nullptr,
           *d_wav = nullptr, *d_tr = nullptr;
     long long *d_off = nullptr;
-    int *d_err = nullptr;  // this shot's device error word (timeouts, non-finite samples)
-    ShotEntry entry;
-    int n0 = 0;  // next step to run
+    int *d_err = nullptr;   // this shot's device error word (timeouts, non-finite samples)
+    int *d_step = nullptr;  // this shot's device step counter (step of a replay's first launch)
+    StepArgs args;          // step constants, fields, source, receivers, decomposition
+    StepMaps maps[2];       // [parity of n]
+    int grid = 0;           // work units per step
+    int n0 = 0;             // next step to run
     Clock::time_point t_submit, t_admit, t_done;
 };
 
@@ -133,12 +97,11 @@ struct sgb_server {
     bool stop = false;
     std::thread th;
     sgb_serve_stats stats;
-    // device table and the graph of the current composition
-    ShotEntry *d_table = nullptr, *h_table = nullptr;
-    int *d_replays = nullptr;  // replays since the last table upload
+    // the graph of the current composition: one branch (stream) per resident shot
     cudaGraphExec_t exec = nullptr;
     bool composition_changed = true;
-    int total_units = 0;
+    cudaStream_t branch[SERVE_MAX_SLOTS] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[SERVE_MAX_SLOTS] = {};
 };
 
 namespace {
@@ -155,10 +118,11 @@ void free_shot_device(sgb_server *sv, Shot *sh)
         cudaFreeAsync(sh->d_off, sv->stream);
         sh->d_off = nullptr;
     }
-    if (sh->d_err) {
-        cudaFreeAsync(sh->d_err, sv->stream);
-        sh->d_err = nullptr;
-    }
+    for (int **p : {&sh->d_err, &sh->d_step})
+        if (*p) {
+            cudaFreeAsync(*p, sv->stream);
+            *p = nullptr;
+        }
 }
 
 // Fields, m, receiver table and step arguments of a newly admitted shot
@@ -184,7 +148,7 @@ int setup_shot(sgb_server *sv, Shot *sh)
         (rc = get((void **)&sh->d_wav, (size_t)sh->nt * 4)) ||
         (rc = get((void **)&sh->d_tr, (size_t)sh->nt * sh->nrec * 4)) ||
         (rc = get((void **)&sh->d_off, (size_t)sh->nrec * 8)) ||
-        (rc = get((void **)&sh->d_err, sizeof(int))))
+        (rc = get((void **)&sh->d_err, sizeof(int))) || (rc = get((void **)&sh->d_step, sizeof(int))))
         return rc;
     std::vector<long long> off(sh->nrec);
     for (int r = 0; r < sh->nrec; ++r)
@@ -194,6 +158,7 @@ int setup_shot(sgb_server *sv, Shot *sh)
     CUDA_TRY(cudaMemcpyAsync(sh->d_wav, sh->wav.data(), (size_t)sh->nt * 4, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(sh->d_off, off.data(), (size_t)sh->nrec * 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemsetAsync(sh->d_err, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(sh->d_step, 0, sizeof(int), st));
     CUDA_TRY(cudaMemsetAsync(sh->u0, 0, fbytes, st));
     CUDA_TRY(cudaMemsetAsync(sh->u1, 0, fbytes, st));
     CUDA_TRY(cudaMemsetAsync(sh->phi, 0, fbytes, st));
@@ -208,7 +173,7 @@ int setup_shot(sgb_server *sv, Shot *sh)
     sh->d_vel = nullptr;
     std::vector<float>().swap(sh->vel);
 
-    StepArgs a;
+    StepArgs &a = sh->args;
     fill_step_constants(&sh->g, L, a);
     a.phi = sh->phi;
     a.err = sh->d_err;
@@ -219,29 +184,12 @@ int setup_shot(sgb_server *sv, Shot *sh)
     a.nrec = sh->nrec;
     a.rec_off = sh->d_off;
     a.traces = sh->d_tr;
-    // z-chunks are planned for the whole batch when it is replayed
-    // (plan_chunks); 32 planes until then.
-    a.tiles_x = (L.Nx + Cfg::BX - 1) / Cfg::BX;
-    a.tiles_y = (L.Ny + Cfg::BY - 1) / Cfg::BY;
-    const int chunks = (L.Nz + 31) / 32;
-    a.zc = (L.Nz + chunks - 1) / chunks;
-    const int grid = a.tiles_x * a.tiles_y * ((L.Nz + a.zc - 1) / a.zc);
-    sh->entry.units = grid;
-    sh->entry.nt = sh->nt;
+    // the shot's own decomposition, as run_shot would choose it
+    choose_decomposition(L.Nx, L.Ny, L.Nz, sv->ds->sms, sv->ds->occ, a, &sh->grid);
     float *buf[2] = {sh->u0, sh->u1};  // buf[0] = u^{-1}, buf[1] = u^0
-    for (int p = 0; p < 2; ++p) {  // step n reads buf[(n+1)&1], writes buf[n&1]
-        sh->entry.args[p] = a;
-        sh->entry.args[p].u_out = buf[p & 1];
-        sh->entry.args[p].u_cur = buf[(p + 1) & 1];
-        StepMaps mp;
-        if ((rc = encode_step_maps<float>(mp, buf[(p + 1) & 1], buf[p & 1], sh->m, sh->phi, L)))
+    for (int p = 0; p < 2; ++p)  // step n reads buf[(n+1)&1], writes buf[n&1]
+        if ((rc = encode_step_maps<float>(sh->maps[p], buf[(p + 1) & 1], buf[p & 1], sh->m, sh->phi, L)))
             return rc;
-        sh->entry.maps[p][0] = mp.ucur;
-        sh->entry.maps[p][1] = mp.ucur_in;
-        sh->entry.maps[p][2] = mp.uprev;
-        sh->entry.maps[p][3] = mp.m;
-        sh->entry.maps[p][4] = mp.phi;
-    }
     sh->n0 = 0;
     return SGB_OK;
 }
@@ -277,73 +225,45 @@ int retire_shot(sgb_server *sv, Shot *sh)
     return rc;
 }
 
-// One z-chunk length for every resident shot: the one that minimises waves x
-// (chunk + priming planes) over this GPU's resident-CTA slots for the whole
-// batch.  A lone small shot gets short chunks that fill the GPU; a full batch
-// gets long ones (fewer priming planes).  The arithmetic of a point does not
-// depend on the decomposition, so results do not change.
-void plan_chunks(sgb_server *sv)
-{
-    const long long slots = (long long)sv->ds->sms * sv->ds->occ;
-    int nz_max = 1;
-    for (Shot *sh : sv->resident) nz_max = std::max(nz_max, sh->L.Nz);
-    int best_zc = std::min(32, nz_max);
-    double best = 1e300;
-    for (int zc = std::min(32, nz_max); zc >= 2; --zc) {
-        long long units = 0;
-        for (Shot *sh : sv->resident) {
-            const StepArgs &a = sh->entry.args[0];
-            units += (long long)a.tiles_x * a.tiles_y * ((sh->L.Nz + zc - 1) / zc);
-        }
-        const double cost = (double)((units + slots - 1) / slots) * (zc + 4);
-        if (cost < best * 0.999) {
-            best = cost;
-            best_zc = zc;
-        }
-    }
-    for (Shot *sh : sv->resident) {
-        const int zc = std::min(best_zc, sh->L.Nz);
-        for (int p = 0; p < 2; ++p) sh->entry.args[p].zc = zc;
-        const StepArgs &a = sh->entry.args[0];
-        sh->entry.units = a.tiles_x * a.tiles_y * ((sh->L.Nz + zc - 1) / zc);
-    }
-}
-
-// Rebuild the device table (and, when the composition changed, the chunk plan
-// and the graph).
+// (Re)capture the replay graph when the composition changed: one branch per
+// resident shot with steps_per_graph launches and the counter increment.
 int prepare_replay(sgb_server *sv)
 {
-    const int ns = (int)sv->resident.size();
-    if (sv->composition_changed || !sv->exec) plan_chunks(sv);
-    int units = 0;
-    for (int i = 0; i < ns; ++i) {
-        Shot *sh = sv->resident[i];
-        sh->entry.unit_begin = units;
-        sh->entry.n0 = sh->n0;
-        units += sh->entry.units;
-        sv->h_table[i] = sh->entry;
-    }
-    CUDA_TRY(cudaMemcpyAsync(sv->d_table, sv->h_table, sizeof(ShotEntry) * ns,
-                             cudaMemcpyHostToDevice, sv->stream));
-    CUDA_TRY(cudaMemsetAsync(sv->d_replays, 0, sizeof(int), sv->stream));
     if (!sv->composition_changed && sv->exec) return SGB_OK;
     if (sv->exec) {
         cudaGraphExecDestroy(sv->exec);
         sv->exec = nullptr;
     }
+    const int S = sv->cfg.steps_per_graph;
     cudaStream_t cs;
     CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
-        for (int i = 0; i < sv->cfg.steps_per_graph && ce == cudaSuccess; ++i) {
-            multi_step_kernel<<<units, Cfg::BLOCK, Stage<Cfg, float>::SMEM_BYTES, cs>>>(
-                sv->d_table, ns, i, sv->d_replays, sv->cfg.steps_per_graph);
-            ce = cudaGetLastError();
-        }
-        if (ce == cudaSuccess) {
-            advance_kernel<<<1, 32, 0, cs>>>(sv->d_replays, 1);
-            ce = cudaGetLastError();
+        ce = cudaEventRecord(sv->ev_fork, cs);
+        for (size_t i = 0; i < sv->resident.size() && ce == cudaSuccess; ++i) {
+            Shot *sh = sv->resident[i];
+            cudaStream_t bs = sv->branch[i];
+            ce = cudaStreamWaitEvent(bs, sv->ev_fork, 0);
+            const StepMaps &p0 = sh->maps[0], &p1 = sh->maps[1];
+            for (int k = 0; k < S && ce == cudaSuccess; ++k) {
+                ShotRun r;
+                r.buf[0] = sh->u0;
+                r.buf[1] = sh->u1;
+                r.step_ptr = sh->d_step;
+                r.step_add = k;
+                r.n_end = sh->nt;
+                shot_step_kernel<Cfg><<<sh->grid, Cfg::BLOCK, Stage<Cfg, float>::SMEM_BYTES, bs>>>(
+                    sh->args, r, p0.ucur, p0.ucur_in, p0.uprev, p0.m, p0.phi, p1.ucur, p1.ucur_in,
+                    p1.uprev, p1.m, p1.phi);
+                ce = cudaGetLastError();
+            }
+            if (ce == cudaSuccess) {
+                advance_kernel<<<1, 32, 0, bs>>>(sh->d_step, S);
+                ce = cudaGetLastError();
+            }
+            if (ce == cudaSuccess) ce = cudaEventRecord(sv->ev_join[i], bs);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, sv->ev_join[i], 0);
         }
         cudaError_t ee = cudaStreamEndCapture(cs, &graph);
         if (ce == cudaSuccess) ce = ee;
@@ -352,7 +272,6 @@ int prepare_replay(sgb_server *sv)
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cs);
     CUDA_TRY(ce);
-    sv->total_units = units;
     sv->composition_changed = false;
     return SGB_OK;
 }
@@ -400,7 +319,7 @@ void scheduler(sgb_server *sv)
             t_prep = ms_between(tp, Clock::now());
             for (int r = 0; r < R && rc == SGB_OK && e == cudaSuccess; ++r)
                 e = cudaGraphLaunch(sv->exec, sv->stream);
-            t_launches += R * (S + 1);
+            t_launches += (int64_t)R * (S + 1) * (int64_t)sv->resident.size();
         }
         tp = Clock::now();
         // 2. meanwhile, set up the admitted shots on the setup stream; they join
@@ -470,6 +389,19 @@ void scheduler(sgb_server *sv)
 
 }  // namespace
 
+// Streams and events of a server (those that were created).
+static void server_release_handles(sgb_server *sv)
+{
+    for (int i = 0; i < SERVE_MAX_SLOTS; ++i) {
+        if (sv->branch[i]) cudaStreamDestroy(sv->branch[i]);
+        if (sv->ev_join[i]) cudaEventDestroy(sv->ev_join[i]);
+    }
+    if (sv->ev_fork) cudaEventDestroy(sv->ev_fork);
+    if (sv->setup_done) cudaEventDestroy(sv->setup_done);
+    if (sv->setup_stream) cudaStreamDestroy(sv->setup_stream);
+    if (sv->stream) cudaStreamDestroy(sv->stream);
+}
+
 extern "C" int serve_footprint(const sgb_grid *g, int32_t nt, int32_t nrec, uint64_t *bytes)
 {
     sgb_layout_info L;
@@ -491,7 +423,7 @@ extern "C" int serve_create(const sgb_serve_config *cfg, sgb_server **out)
     DevState *ds;
     int rc = device_state(&ds);
     if (rc) return rc;
-    CUDA_TRY(cudaFuncSetAttribute(multi_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CUDA_TRY(cudaFuncSetAttribute(shot_step_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)Stage<Cfg, float>::SMEM_BYTES));
     sgb_server *sv = new sgb_server();
     sv->cfg = *cfg;
@@ -501,18 +433,13 @@ extern "C" int serve_create(const sgb_serve_config *cfg, sgb_server **out)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->setup_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->setup_done, cudaEventDisableTiming);
-    if (e == cudaSuccess)
-        e = cudaMalloc((void **)&sv->d_table, sizeof(ShotEntry) * SERVE_MAX_SLOTS);
-    if (e == cudaSuccess)
-        e = cudaMallocHost((void **)&sv->h_table, sizeof(ShotEntry) * SERVE_MAX_SLOTS);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&sv->d_replays, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < cfg->max_slots && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&sv->branch[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_join[i], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
-        if (sv->d_table) cudaFree(sv->d_table);
-        if (sv->d_replays) cudaFree(sv->d_replays);
-        if (sv->h_table) cudaFreeHost(sv->h_table);
-        if (sv->stream) cudaStreamDestroy(sv->stream);
-        if (sv->setup_stream) cudaStreamDestroy(sv->setup_stream);
-        if (sv->setup_done) cudaEventDestroy(sv->setup_done);
+        server_release_handles(sv);
         delete sv;
         return fail(e == cudaErrorMemoryAllocation ? SGB_ERR_OUT_OF_MEMORY : SGB_ERR_CUDA,
                     "serve_create: %s", cudaGetErrorString(e));
@@ -638,12 +565,7 @@ extern "C" int serve_destroy(sgb_server *sv)
     if (sv->exec) cudaGraphExecDestroy(sv->exec);
     cudaStreamSynchronize(sv->stream);
     cudaStreamSynchronize(sv->setup_stream);
-    cudaFree(sv->d_table);
-    cudaFree(sv->d_replays);
-    cudaFreeHost(sv->h_table);
-    cudaEventDestroy(sv->setup_done);
-    cudaStreamDestroy(sv->setup_stream);
-    cudaStreamDestroy(sv->stream);
+    server_release_handles(sv);
     delete sv;
     return SGB_OK;
 }

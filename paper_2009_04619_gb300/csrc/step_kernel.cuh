@@ -348,13 +348,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // Launch variants of the step: one launch per step over the standard units;
 // the shell launches of a temporally blocked pair (units from a table, no store
 // inside the two-step kernel's box); the persistent dataflow launch (CTAs take
-// (step, unit) items in turn, ring slots counted across units).
-enum : int { VAR_PLAIN = 0, VAR_SHELL = 1, VAR_FLOW = 2 };
+// (step, unit) items in turn, ring slots counted across units); one launch per
+// step whose output buffer is chosen on the device by the parity of the step
+// (CUDA-graph replays that do not repeat with the buffer parity).
+enum : int { VAR_PLAIN = 0, VAR_SHELL = 1, VAR_FLOW = 2, VAR_PARITY = 3 };
 
 // Per-thread state of one fused-step work unit (a tile x a z-chunk).
 template <class C, class T, int MODE = MODE_FWD, int VAR = VAR_PLAIN>
 struct StepCta {
     static constexpr bool SHELL = VAR == VAR_SHELL, FLOW = VAR == VAR_FLOW;
+    static constexpr bool OUTV = VAR == VAR_FLOW || VAR == VAR_PARITY;  // output via u_out_v
     using E = Elem<T>;
     using G = Stage<C, T, MODE>;
     // the adjoint's PML-path band is one point wider: inner points next to the
@@ -379,7 +382,7 @@ struct StepCta {
                     // x-PML (planes outside the z-PML load only these); 0 otherwise
     int phoff;      // offset of this thread's row-0 quad in the blocked phi tile
     int useq, pseq;  // FLOW: u and (u^{n-1}, m, phi) planes of earlier units of this CTA
-    void *u_out_v;   // FLOW: the output buffer of the current item's step
+    void *u_out_v;   // FLOW, PARITY: the output buffer of the current step
     float s_cur, s_prev, inv_s_next;  // fp16 scales (1 otherwise)
     float vmax;                       // running max |u^{n+1}| of this thread
     // PML terms of the thread's fixed columns i = gi + e and rows j = gj0 + r:
@@ -730,7 +733,7 @@ struct StepCta {
                                              fmaxf(fabsf(un.z), fabsf(un.w))));
                     un = f4mul(inv_s_next, un);
                 }
-                T *uo = static_cast<T *>(FLOW ? u_out_v : a.u_out) + off;
+                T *uo = static_cast<T *>(OUTV ? u_out_v : a.u_out) + off;
                 const bool wphi = PML && any_pml;  // phi^{n+1}, or mu^k in the adjoint
                 if (gi + 3 < a.Nx) {
                     E::st(uo, un, rnd);
@@ -905,7 +908,8 @@ struct StepMapPtrs {
 // launch after a shot's last step).
 template <class C, class T, int MODE = MODE_FWD, int VAR = VAR_PLAIN>
 __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &tm, int unit,
-                                          int units, int n, bool sample_only)
+                                          int units, int n, bool sample_only,
+                                          void *u_out_v = nullptr, const void *u_cur_v = nullptr)
 {
     using S = StepCta<C, T, MODE, VAR>;
     constexpr bool SHELL = VAR == VAR_SHELL;
@@ -939,6 +943,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     const int tid = threadIdx.x;
     st.tid = tid;
     st.lane = tid & 31;
+    st.u_out_v = u_out_v;
 
     // Work unit: chunk-major so that CTAs running together share z and their
     // x-y halos meet in L2.
@@ -979,7 +984,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
 
     // Receivers of the previous step: u^n is read-only in this launch.
     if (a.nrec > 0 && n >= 1) {
-        const T *uc = static_cast<const T *>(a.u_cur);
+        const T *uc = static_cast<const T *>(S::OUTV ? u_cur_v : a.u_cur);
         for (int r = unit * C::BLOCK + tid; r < a.nrec; r += units * C::BLOCK) {
             const float v = Elem<T>::get(uc + a.rec_off[r]) * st.s_cur;
             a.traces[(long long)(n - 1) * a.nrec + r] = v;
@@ -1053,6 +1058,43 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     step_unit<C, float, MODE_FWD, VAR_SHELL>(a, tm, blockIdx.x, gridDim.x, n, false);
+}
+
+// One step of one shot inside a CUDA-graph replay: the step n = *step_ptr +
+// step_add comes from a device counter, the buffers and tensor maps of its
+// parity are chosen here (so a replay of any length repeats), and launches past
+// the shot's last step do nothing (n_end: the last launch, which only samples
+// the receivers of step n_end - 1).
+struct ShotRun {
+    void *buf[2];         // step n reads buf[(n + 1) & 1] and writes buf[n & 1]
+    const int *step_ptr;  // the shot's device step counter
+    int step_add;
+    int n_end;
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::BLOCK, C::MINB)
+    shot_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ ShotRun r,
+                     const __grid_constant__ CUtensorMap m0_ucur,
+                     const __grid_constant__ CUtensorMap m0_ucur_in,
+                     const __grid_constant__ CUtensorMap m0_uprev,
+                     const __grid_constant__ CUtensorMap m0_m,
+                     const __grid_constant__ CUtensorMap m0_phi,
+                     const __grid_constant__ CUtensorMap m1_ucur,
+                     const __grid_constant__ CUtensorMap m1_ucur_in,
+                     const __grid_constant__ CUtensorMap m1_uprev,
+                     const __grid_constant__ CUtensorMap m1_m,
+                     const __grid_constant__ CUtensorMap m1_phi)
+{
+    const int n = *r.step_ptr + r.step_add;
+    if (n > r.n_end) return;  // finished: waits for retirement
+    const bool odd = n & 1;
+    const StepMapPtrs tm = odd ? StepMapPtrs{&m1_ucur, &m1_ucur_in, &m1_uprev, &m1_m, &m1_phi,
+                                             nullptr, nullptr}
+                               : StepMapPtrs{&m0_ucur, &m0_ucur_in, &m0_uprev, &m0_m, &m0_phi,
+                                             nullptr, nullptr};
+    step_unit<C, float, MODE_FWD, VAR_PARITY>(a, tm, blockIdx.x, gridDim.x, n, n == r.n_end,
+                                              r.buf[n & 1], r.buf[(n + 1) & 1]);
 }
 
 // Forward step that also stores g^n = L u^n + phi^n + f^n (adjoint recomputation).
