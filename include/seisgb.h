@@ -39,6 +39,7 @@ extern "C" {
 #define SGB_ERR_TIMEOUT (-5)
 #define SGB_ERR_NONFINITE (-6)
 #define SGB_ERR_REJECTED (-7)
+#define SGB_ERR_CANCELLED (-8)
 
 /* Wavefield storage formats (arithmetic is always fp32). */
 #define SGB_FP32 0
@@ -185,6 +186,24 @@ int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int
              const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec, float *traces,
              float *final_u, void *stream);
 
+/* Steps n_begin .. n_end-1 of a shot (Algorithm 1), resumable: the state
+ * before step n_begin -- u_cur = u^{n_begin}, u_prev = u^{n_begin - 1}, phi =
+ * phi^{n_begin}, each Nz*Ny*Nx fp32 compact, host or device -- is read, and
+ * overwritten with the state before step n_end.  Zero arrays at n_begin = 0
+ * start a shot.  A shot run as segments [0, k), [k, nt) with the state passed
+ * along gives the same bits as run_shot over [0, nt), whatever k (the source
+ * and, for bf16, the stochastic rounding use the absolute step).  Stored
+ * fields round to g->storage (SGB_FP32 or SGB_BF16; SGB_FP16_SCALED is
+ * rejected: its scale is not part of the state).  wavelet holds samples for
+ * the absolute steps (at least n_end); traces receives n_end - n_begin rows,
+ * traces[(n - n_begin)*nrec + r] = u^{n+1}(rec_r).  SGB_SCHED_PAIRS runs as
+ * SGB_SCHED_STEP here.  Otherwise as run_shot (the state arrays may not
+ * overlap each other, velocity, wavelet or traces). */
+int run_shot_segment(const sgb_grid *g, const float *velocity, const float *wavelet,
+                     int32_t n_begin, int32_t n_end, const int32_t *src_ijk,
+                     const int32_t *rec_ijk, int32_t nrec, float *traces, float *u_cur,
+                     float *u_prev, float *phi, void *stream);
+
 /* Trace misfit J = 1/2 sum_{n,r} (d^n_r - observed^n_r)^2 of a shot (d as in
  * run_shot) and its gradient dJ/dv with respect to the velocity model, by the
  * exact discrete adjoint of the fused step including the PML and the source
@@ -270,8 +289,8 @@ typedef struct {
     int32_t status;             /* SGB_OK or the error that ended the shot:
                                    TIMEOUT (a kernel wait gave up), NONFINITE (a
                                    receiver sampled NaN/Inf), OUT_OF_MEMORY,
-                                   CUDA_ERROR; each shot has its own device
-                                   error word */
+                                   CUDA_ERROR, CANCELLED (serve_cancel); each
+                                   shot has its own device error word */
     int32_t nt, nrec;
     float *traces;              /* caller buffer of nt*nrec floats (or NULL);
                                    filled when serve_poll returns SGB_OK and
@@ -290,6 +309,7 @@ typedef struct {
      * table and re-capturing the replay graph, retiring finished shots, and
      * waiting for enqueued replays to finish */
     double setup_ms, prepare_ms, retire_ms, wait_ms;
+    uint64_t cancelled;         /* requests ended by serve_cancel */
 } sgb_serve_stats;
 
 typedef struct sgb_server sgb_server;
@@ -308,6 +328,12 @@ int serve_submit(sgb_server *s, const sgb_shot_request *req, uint64_t *ticket);
  * is then forgotten).  SGB_PENDING: not done and timeout_us == 0.
  * SGB_ERR_TIMEOUT: not done within timeout_us (> 0).  INVALID_ARG: unknown. */
 int serve_poll(sgb_server *s, uint64_t ticket, sgb_shot_result *out, int32_t timeout_us);
+/* Cancel a request.  Queued: it ends at once with status SGB_ERR_CANCELLED.
+ * Admitted: it is retired when the replays already enqueued finish (its
+ * device memory returns to the pool; no traces).  Finished already: no effect
+ * (its result stands).  The result is collected with serve_poll as usual.
+ * INVALID_ARG for an unknown ticket. */
+int serve_cancel(sgb_server *s, uint64_t ticket);
 /* Copy of the server's counters (taken under the server's lock, so the fields
  * are consistent with each other); INVALID_ARG if s or out is NULL. */
 int serve_stats(sgb_server *s, sgb_serve_stats *out);
@@ -336,6 +362,19 @@ int sgb_device_status(void *stream);
  * value is SGB_OK unless the arguments are invalid or the launch failed.  No
  * GPU fault is involved and the context stays usable.  Synchronises stream. */
 int sgb_selftest_wait_timeout(int32_t limit_us, int32_t *status_out, void *stream);
+
+/* Test hook (no counterpart in the paper; process-wide): counting the
+ * library's device-pool allocations from this call on, numbers after ..
+ * after + count - 1 fail with SGB_ERR_OUT_OF_MEMORY as an exhausted device
+ * would (host-side: no device fault is involved); the others succeed.  count
+ * 0 disarms.  Calls that fail this way leave no partial state: their scratch
+ * returns to the pool; a served shot whose set-up fails ends with status
+ * SGB_ERR_OUT_OF_MEMORY and the others run on. */
+int sgb_debug_fail_allocations(int64_t after, int64_t count);
+
+/* Bytes currently allocated from the current device's library pool (scratch
+ * of calls in flight, resident served shots). */
+int sgb_pool_used_bytes(int64_t *bytes);
 
 /* Number of this library's kernels launched by the calling thread since the
  * last reset (graph replays count every kernel node). */

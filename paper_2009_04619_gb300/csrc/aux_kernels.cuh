@@ -29,6 +29,24 @@ __global__ void pack_kernel(PadGeom g, const float *__restrict__ src, float *__r
     }
 }
 
+// compact fp32 (Nz, Ny, Nx) -> padded field of storage T (rounded to nearest);
+// halo and row padding receive zeros.
+template <class T>
+__global__ void pack_t_kernel(PadGeom g, const float *__restrict__ src, T *__restrict__ dst,
+                              long long elems)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < elems; p += stride) {
+        const long long kk = p / g.sxy, rem = p - kk * g.sxy;
+        const long long jj = rem / g.sx, ii = rem - jj * g.sx;
+        const long long i = ii - 8, j = jj - 4, k = kk - 4;
+        float v = 0.0f;
+        if (i >= 0 && i < g.Nx && j >= 0 && j < g.Ny && k >= 0 && k < g.Nz)
+            v = src[(k * g.Ny + j) * g.Nx + i];
+        dst[p] = T(v);
+    }
+}
+
 // padded -> compact
 __global__ void unpack_kernel(PadGeom g, const float *__restrict__ src, float *__restrict__ dst)
 {

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
             for (int r = f.rec_start[unit] + tid; r < f.rec_start[unit + 1]; r += THREADS) {
                 const int ri = f.rec_list[r];
                 const float v = ld_cg_value(uo + a.rec_off[ri]);
-                a.traces[(long long)n * a.nrec + ri] = v;
+                a.traces[(long long)(n - a.rec_n0) * a.nrec + ri] = v;
                 if (!isfinite(v)) atomicOr(a.err, DEV_ERR_NONFINITE);
             }
         }

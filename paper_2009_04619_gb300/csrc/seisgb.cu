@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -57,6 +58,31 @@ extern "C" int64_t sgb_launch_count(int reset)
     int64_t v = t_launches;
     if (reset) t_launches = 0;
     return v;
+}
+
+// Host-side fault injection (a test hook, process-wide): the library's pool
+// allocations are numbered from the moment the hook is armed; numbers
+// [after, after + count) fail as out of memory, the others succeed.
+static std::mutex g_inject_mu;
+static long long g_inject_seen = 0, g_inject_after = 0, g_inject_count = 0;
+
+// True when the armed hook says this allocation fails.
+static bool injected_alloc_failure()
+{
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    if (g_inject_count <= 0) return false;
+    const long long k = g_inject_seen++;
+    return k >= g_inject_after && k < g_inject_after + g_inject_count;
+}
+
+extern "C" int sgb_debug_fail_allocations(int64_t after, int64_t count)
+{
+    if (after < 0 || count < 0) return fail(SGB_ERR_INVALID_ARG, "after and count must be >= 0");
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_seen = 0;
+    g_inject_after = after;
+    g_inject_count = count;
+    return SGB_OK;
 }
 
 // Device error word of stencil_step (bounded-wait timeouts, non-finite
@@ -352,6 +378,8 @@ struct Scratch {
     }
     int get(void **p, size_t bytes)
     {
+        if (injected_alloc_failure())
+            return fail(SGB_ERR_OUT_OF_MEMORY, "scratch allocation of %zu bytes failed (injected)", bytes);
         cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -517,6 +545,18 @@ extern "C" int sgb_selftest_wait_timeout(int32_t limit_us, int32_t *status_out, 
     CUDA_TRY(cudaMemcpyAsync(&v, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     *status_out = (v & DEV_ERR_TIMEOUT) ? SGB_ERR_TIMEOUT : v ? SGB_ERR_CUDA : SGB_OK;
+    return SGB_OK;
+}
+
+extern "C" int sgb_pool_used_bytes(int64_t *bytes)
+{
+    if (!bytes) return fail(SGB_ERR_INVALID_ARG, "bytes is NULL");
+    DevState *ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    cuuint64_t v = 0;
+    CUDA_TRY(cudaMemPoolGetAttribute(ds->pool, cudaMemPoolAttrUsedMemCurrent, &v));
+    *bytes = (int64_t)v;
     return SGB_OK;
 }
 
@@ -853,8 +893,8 @@ int prepare_flow(int *occ)
 // tensor maps and buffers of steps of parity p (step n writes buf[n & 1]).
 template <class T>
 int run_flow(const sgb_layout_info &L, DevState *ds, cudaStream_t st, Scratch &sc,
-             const StepArgs &base, const StepMaps (&maps)[2], void *const (&buf)[2], int nt,
-             const int32_t *rec_ijk, int nrec)
+             const StepArgs &base, const StepMaps (&maps)[2], void *const (&buf)[2], int n_begin,
+             int n_end, const int32_t *rec_ijk, int nrec)
 {
     int rc, occ = 0;
     if ((rc = prepare_flow<T>(&occ))) return rc;
@@ -888,7 +928,11 @@ int run_flow(const sgb_layout_info &L, DevState *ds, cudaStream_t st, Scratch &s
     if ((rc = sc.get((void **)&d_done, (size_t)units * 4)) || (rc = sc.get((void **)&d_counter, 16)) ||
         (rc = sc.get((void **)&d_rs, rs.size() * 4)) || (rc = sc.get((void **)&d_rl, rl.size() * 4)))
         return rc;
-    CUDA_TRY(cudaMemsetAsync(d_done, 0, (size_t)units * 4, st));
+    {  // every unit has completed n_begin steps when the launch starts
+        std::vector<int> d0(units, n_begin);
+        CUDA_TRY(cudaMemcpyAsync(d_done, d0.data(), (size_t)units * 4, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));  // d0 is a pageable temporary
+    }
     CUDA_TRY(cudaMemsetAsync(d_counter, 0, 4, st));
     CUDA_TRY(cudaMemcpyAsync(d_rs, rs.data(), rs.size() * 4, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(d_rl, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
@@ -902,8 +946,8 @@ int run_flow(const sgb_layout_info &L, DevState *ds, cudaStream_t st, Scratch &s
     f.units = units;
     f.tiles_x = fa.tiles_x;
     f.tiles_y = fa.tiles_y;
-    f.n_begin = 0;
-    f.n_end = nt;
+    f.n_begin = n_begin;
+    f.n_end = n_end;
     f.counter = d_counter;
     f.done = d_done;
     f.rec_start = d_rs;
@@ -922,12 +966,16 @@ int run_flow(const sgb_layout_info &L, DevState *ds, cudaStream_t st, Scratch &s
 // Shot time loop and outputs for wavefield storage T (run_shot after its
 // argument checks and the CFL check).
 template <class T>
+// Steps n_begin .. n_end-1; state: null (start from zero fields) or three
+// device compact fp32 arrays (u^n, u^{n-1}, phi^n) read at n_begin and
+// overwritten with the state at n_end.  Traces rows are steps n_begin ...
 int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
-               Scratch &sc, const float *d_vel, const float *d_wav, int nt,
+               Scratch &sc, const float *d_vel, const float *d_wav, int n_begin, int n_end,
                const int32_t *src_ijk, const int32_t *rec_ijk, int nrec, const long long *d_off,
-               float *d_tr, float *final_u, int *d_err)
+               float *d_tr, float *final_u, float *const *state, int *d_err)
 {
     int rc;
+    const int nt = n_end, nsteps = n_end - n_begin;
     const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
     const size_t ubytes = (size_t)L.elems * sizeof(T), fbytes = (size_t)L.elems * 4;
     void *u0, *u1;
@@ -938,11 +986,23 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         (rc = sc.get((void **)&phi, fbytes)) || (rc = sc.get((void **)&m, fbytes)) ||
         (rc = sc.get((void **)&d_step, sizeof(int))))
         return rc;
-    CUDA_TRY(cudaMemsetAsync(d_step, 0, sizeof(int), st));
-    CUDA_TRY(cudaMemsetAsync(u0, 0, ubytes, st));
-    CUDA_TRY(cudaMemsetAsync(u1, 0, ubytes, st));
-    CUDA_TRY(cudaMemsetAsync(phi, 0, fbytes, st));
+    CUDA_TRY(cudaMemcpyAsync(d_step, &n_begin, sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemsetAsync(m, 0, fbytes, st));
+    if (!state) {
+        CUDA_TRY(cudaMemsetAsync(u0, 0, ubytes, st));
+        CUDA_TRY(cudaMemsetAsync(u1, 0, ubytes, st));
+        CUDA_TRY(cudaMemsetAsync(phi, 0, fbytes, st));
+    } else {  // u^n into buf[(n+1)&1], u^{n-1} into buf[n&1] (n = n_begin), phi^n
+        void *bb[2] = {u0, u1};
+        const int eg = ew_grid(L.elems, *ds);
+        pack_t_kernel<T><<<eg, 256, 0, st>>>(pad_geom(L), state[0], static_cast<T *>(bb[(n_begin + 1) & 1]),
+                                             L.elems);
+        pack_t_kernel<T><<<eg, 256, 0, st>>>(pad_geom(L), state[1], static_cast<T *>(bb[n_begin & 1]),
+                                             L.elems);
+        pack_kernel<<<eg, 256, 0, st>>>(pad_geom(L), state[2], phi, L.elems);
+        CUDA_TRY(cudaGetLastError());
+        t_launches += 3;
+    }
     if (Elem<T>::SCALED) {
         if ((rc = sc.get((void **)&ss, sizeof(ScaleState)))) return rc;
         static const ScaleState init = {{1.0f, 1.0f, 1.0f, 1.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
@@ -971,6 +1031,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     base.nrec = nrec;
     base.rec_off = d_off;
     base.traces = d_tr;
+    base.rec_n0 = n_begin;
     const int occ = std::is_same<T, float>::value ? ds->occ
                     : std::is_same<T, __half>::value ? ds->occ_h : ds->occ_b;
     int grid = 0;
@@ -990,13 +1051,14 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
 
     bool looped = false;
     if constexpr (!Elem<T>::SCALED) {
-        if (resolve_schedule(g) == SGB_SCHED_FLOW && nt > 0) {
-            if ((rc = run_flow<T>(L, ds, st, sc, base, maps, buf, nt, rec_ijk, nrec))) return rc;
+        if (resolve_schedule(g) == SGB_SCHED_FLOW && nsteps > 0) {
+            if ((rc = run_flow<T>(L, ds, st, sc, base, maps, buf, n_begin, n_end, rec_ijk, nrec)))
+                return rc;
             looped = true;
         }
     }
     const int GS = 32;  // steps per graph replay (even: the buffer parity repeats)
-    const int replays = looped ? 0 : nt / GS;
+    const int replays = looped ? 0 : nsteps / GS;
     if (replays > 0) {
         cudaStream_t cs;
         CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1006,7 +1068,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
             for (int i = 0; i < GS && crc == SGB_OK; ++i)
-                crc = launch_step<T>(args_for(i, d_step, i), maps[i & 1], grid, cs);
+                crc = launch_step<T>(args_for(n_begin + i, d_step, i), maps[(n_begin + i) & 1], grid, cs);
             if (crc == SGB_OK) {
                 advance_kernel<<<1, 32, 0, cs>>>(d_step, GS);
                 ce = cudaGetLastError();
@@ -1028,18 +1090,27 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         if (crc) return crc;
         CUDA_TRY(ce);
     }
-    for (int n = looped ? nt : replays * GS; n < nt; ++n)
+    for (int n = looped ? n_end : n_begin + replays * GS; n < n_end; ++n)
         if ((rc = launch_step<T>(args_for(n, nullptr, n), maps[n & 1], grid, st))) return rc;
 
-    // u^{nt}: written by step nt-1 into buf[(nt-1)&1] (u^0 = buf[1] when nt = 0)
-    const void *u_final_dev = nt > 0 ? buf[(nt - 1) & 1] : buf[1];
+    // u^k lives in buf[(k+1)&1] (written by step k-1): u^{nt} in buf[(nt+1)&1]
+    const void *u_final_dev = buf[(nt + 1) & 1];
     const float *s_final = ss ? &ss->s[nt & 3] : nullptr;
-    if (nrec > 0 && nt > 0 && !looped) {  // the dataflow launch sampled every row itself
+    if (nrec > 0 && nsteps > 0 && !looped) {  // the dataflow launch sampled every row itself
         gather_t_kernel<T><<<(nrec + 255) / 256, 256, 0, st>>>(
             static_cast<const T *>(u_final_dev), d_off, nrec, s_final,
-            d_tr + (size_t)(nt - 1) * nrec, d_err);
+            d_tr + (size_t)(nsteps - 1) * nrec, d_err);
         CUDA_TRY(cudaGetLastError());
         ++t_launches;
+    }
+    if (state) {  // the state at n_end: u^{nt}, u^{nt-1}, phi^{nt}
+        unpack_t_kernel<T><<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L),
+            static_cast<const T *>(u_final_dev), s_final, state[0]);
+        unpack_t_kernel<T><<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L),
+            static_cast<const T *>(buf[nt & 1]), nullptr, state[1]);
+        unpack_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), phi, state[2]);
+        CUDA_TRY(cudaGetLastError());
+        t_launches += 3;
     }
     if (final_u) {
         const bool host_u = !is_device_ptr(final_u);
@@ -1250,18 +1321,27 @@ extern "C" int stencil_step2(const sgb_grid *g, const float *u_prev, const float
     return launch_pair(g, pp, pm, d_units, base, u_next, u_next2, u_cur, nullptr, step, st);
 }
 
-extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
-                        const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec,
-                        float *traces, float *final_u, void *stream)
+namespace {
+
+// run_shot and run_shot_segment: steps n_begin .. n_end-1; state (u^n,
+// u^{n-1}, phi^n compact fp32, host or device) or null for zero fields and no
+// state out.
+int run_shot_common(const sgb_grid *g, const float *velocity, const float *wavelet, int n_begin,
+                    int n_end, const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec,
+                    float *traces, float *final_u, float *const *state, void *stream)
 {
     sgb_layout_info L;
     int rc = check_grid(g, &L);
     if (rc) return rc;
+    const int nt = n_end, nsteps = n_end - n_begin;
     if (!velocity) return fail(SGB_ERR_INVALID_ARG, "velocity is NULL");
-    if (nt < 0) return fail(SGB_ERR_INVALID_ARG, "nt must be >= 0");
-    if (nt > 0 && src_ijk && !wavelet) return fail(SGB_ERR_INVALID_ARG, "wavelet is NULL");
+    if (n_begin < 0 || nsteps < 0) return fail(SGB_ERR_INVALID_ARG, "steps must satisfy 0 <= n_begin <= n_end");
+    if (nsteps > 0 && src_ijk && !wavelet) return fail(SGB_ERR_INVALID_ARG, "wavelet is NULL");
     if (nrec < 0) return fail(SGB_ERR_INVALID_ARG, "nrec < 0");
-    if (nrec > 0 && (!rec_ijk || !traces)) return fail(SGB_ERR_INVALID_ARG, "receiver arrays NULL");
+    if (nrec > 0 && (!rec_ijk || (nsteps > 0 && !traces)))
+        return fail(SGB_ERR_INVALID_ARG, "receiver arrays NULL");
+    if (state && g->storage == SGB_FP16_SCALED)
+        return fail(SGB_ERR_INVALID_ARG, "shot segments need SGB_FP32 or SGB_BF16 storage");
     if (src_ijk && !in_inner(g, src_ijk[0], src_ijk[1], src_ijk[2]))
         return fail(SGB_ERR_INVALID_ARG, "source (%d,%d,%d) outside the inner region", src_ijk[0],
                     src_ijk[1], src_ijk[2]);
@@ -1274,12 +1354,16 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
         off[r] = L.origin + (long long)k * L.stride_z + (long long)j * L.sx + i;
     }
     const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
+    const size_t cb = (size_t)ncomp * 4;
     {
-        const Span ins[] = {{velocity, (size_t)ncomp * 4, "velocity"},
+        const Span ins[] = {{velocity, cb, "velocity"},
                             {src_ijk ? wavelet : nullptr, (size_t)nt * 4, "wavelet"}};
-        const Span outs[] = {{nrec > 0 ? traces : nullptr, (size_t)nt * nrec * 4, "traces"},
-                             {final_u, (size_t)ncomp * 4, "final_u"}};
-        if ((rc = check_no_overlap(outs, 2, ins, 2))) return rc;
+        const Span outs[] = {{nrec > 0 ? traces : nullptr, (size_t)nsteps * nrec * 4, "traces"},
+                             {final_u, cb, "final_u"},
+                             {state ? state[0] : nullptr, cb, "state u^n"},
+                             {state ? state[1] : nullptr, cb, "state u^{n-1}"},
+                             {state ? state[2] : nullptr, cb, "state phi^n"}};
+        if ((rc = check_no_overlap(outs, 5, ins, 2))) return rc;
     }
     DevState *ds;
     if ((rc = device_state(&ds))) return rc;
@@ -1292,8 +1376,8 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     const float *d_vel = velocity;
     if (!is_device_ptr(velocity)) {
         float *t;
-        if ((rc = sc.get((void **)&t, (size_t)ncomp * 4))) return rc;
-        CUDA_TRY(cudaMemcpyAsync(t, velocity, (size_t)ncomp * 4, cudaMemcpyHostToDevice, st));
+        if ((rc = sc.get((void **)&t, cb))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(t, velocity, cb, cudaMemcpyHostToDevice, st));
         d_vel = t;
     }
     // velocity range -> CFL check against the model's actual maximum
@@ -1323,38 +1407,76 @@ extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *w
     }
     float *d_tr = traces;
     const bool host_traces = nrec > 0 && !is_device_ptr(traces);
-    if (host_traces && nt > 0) {
-        if ((rc = sc.get((void **)&d_tr, (size_t)nt * nrec * 4))) return rc;
+    if (host_traces && nsteps > 0) {
+        if ((rc = sc.get((void **)&d_tr, (size_t)nsteps * nrec * 4))) return rc;
     }
     long long *d_off = nullptr;
     if (nrec > 0) {
         if ((rc = sc.get((void **)&d_off, (size_t)nrec * 8))) return rc;
         CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), (size_t)nrec * 8, cudaMemcpyHostToDevice, st));
     }
+    // the state on the device (host arrays are staged through scratch)
+    float *d_state[3] = {nullptr, nullptr, nullptr};
+    bool host_state[3] = {false, false, false};
+    if (state) {
+        for (int q = 0; q < 3; ++q) {
+            d_state[q] = state[q];
+            if (!is_device_ptr(state[q])) {
+                host_state[q] = true;
+                if ((rc = sc.get((void **)&d_state[q], cb))) return rc;
+                CUDA_TRY(cudaMemcpyAsync(d_state[q], state[q], cb, cudaMemcpyHostToDevice, st));
+            }
+        }
+    }
+    float *const *dst = state ? d_state : nullptr;
     switch (g->storage) {
     case SGB_FP16_SCALED:
-        rc = run_shot_t<__half>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, rec_ijk, nrec, d_off, d_tr,
-                                final_u, d_err);
+        rc = run_shot_t<__half>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end, src_ijk, rec_ijk,
+                                nrec, d_off, d_tr, final_u, dst, d_err);
         break;
     case SGB_BF16:
-        rc = run_shot_t<__nv_bfloat16>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, rec_ijk, nrec,
-                                       d_off, d_tr, final_u, d_err);
+        rc = run_shot_t<__nv_bfloat16>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end, src_ijk,
+                                       rec_ijk, nrec, d_off, d_tr, final_u, dst, d_err);
         break;
     default:
-        if (g->schedule == SGB_SCHED_PAIRS)
+        // temporal blocking covers whole shots; a segment takes one step per launch
+        if (g->schedule == SGB_SCHED_PAIRS && !state && n_begin == 0)
             rc = run_shot_pairs(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, nrec, d_off, d_tr,
                                 final_u, d_err);
         else
-            rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, nt, src_ijk, rec_ijk, nrec,
-                                   d_off, d_tr, final_u, d_err);
+            rc = run_shot_t<float>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end, src_ijk, rec_ijk,
+                                   nrec, d_off, d_tr, final_u, dst, d_err);
     }
     if (rc) return rc;
-    if (host_traces && nt > 0)
-        CUDA_TRY(cudaMemcpyAsync(traces, d_tr, (size_t)nt * nrec * 4, cudaMemcpyDeviceToHost, st));
+    if (host_traces && nsteps > 0)
+        CUDA_TRY(cudaMemcpyAsync(traces, d_tr, (size_t)nsteps * nrec * 4, cudaMemcpyDeviceToHost, st));
+    for (int q = 0; q < 3; ++q)
+        if (host_state[q]) CUDA_TRY(cudaMemcpyAsync(state[q], d_state[q], cb, cudaMemcpyDeviceToHost, st));
     int dev_err = 0;
     CUDA_TRY(cudaMemcpyAsync(&dev_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return dev_err_status(dev_err);
+}
+
+}  // namespace
+
+extern "C" int run_shot(const sgb_grid *g, const float *velocity, const float *wavelet, int32_t nt,
+                        const int32_t *src_ijk, const int32_t *rec_ijk, int32_t nrec,
+                        float *traces, float *final_u, void *stream)
+{
+    return run_shot_common(g, velocity, wavelet, 0, nt, src_ijk, rec_ijk, nrec, traces, final_u,
+                           nullptr, stream);
+}
+
+extern "C" int run_shot_segment(const sgb_grid *g, const float *velocity, const float *wavelet,
+                                int32_t n_begin, int32_t n_end, const int32_t *src_ijk,
+                                const int32_t *rec_ijk, int32_t nrec, float *traces, float *u_cur,
+                                float *u_prev, float *phi, void *stream)
+{
+    if (!u_cur || !u_prev || !phi) return fail(SGB_ERR_INVALID_ARG, "state arrays NULL");
+    float *const state[3] = {u_cur, u_prev, phi};
+    return run_shot_common(g, velocity, wavelet, n_begin, n_end, src_ijk, rec_ijk, nrec, traces,
+                           nullptr, state, stream);
 }
 
 // ---------------------------------------------------------------------------

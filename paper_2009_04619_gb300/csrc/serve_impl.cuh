@@ -58,6 +58,7 @@ struct Shot {
     std::vector<int32_t> rec;
     uint64_t footprint = 0;
     int status = SGB_OK;
+    std::atomic<bool> cancel{false};  // serve_cancel on an admitted shot
     // device
     float *u0 = nullptr, *u1 = nullptr, *phi = nullptr, *m = nullptr, *d_vel = nullptr,
           *d_wav = nullptr, *d_tr = nullptr;
@@ -93,6 +94,7 @@ struct sgb_server {
     std::vector<Shot *> resident;
     std::map<uint64_t, Shot *> done;
     std::map<uint64_t, bool> known;  // ticket -> pending
+    std::map<uint64_t, Shot *> live; // submitted, not yet done
     uint64_t next_ticket = 1, budget_used = 0;
     bool stop = false;
     std::thread th;
@@ -134,6 +136,8 @@ int setup_shot(sgb_server *sv, Shot *sh)
     const size_t fbytes = (size_t)L.elems * 4;
     const long long ncomp = (long long)L.Nx * L.Ny * L.Nz;
     auto get = [&](void **p, size_t b) -> int {
+        if (injected_alloc_failure())
+            return fail(SGB_ERR_OUT_OF_MEMORY, "serve: allocation of %zu bytes failed (injected)", b);
         cudaError_t e = cudaMallocFromPoolAsync(p, b ? b : 16, sv->ds->pool, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -201,6 +205,7 @@ int retire_shot(sgb_server *sv, Shot *sh)
 {
     sh->traces.resize((size_t)sh->nt * sh->nrec);
     int rc = SGB_OK;
+    if (sh->status == SGB_OK && sh->cancel) sh->status = SGB_ERR_CANCELLED;
     if (sh->status == SGB_OK) {
         int v = 0;
         cudaError_t e = cudaMemcpyAsync(&v, sh->d_err, sizeof(int), cudaMemcpyDeviceToHost,
@@ -336,6 +341,7 @@ void scheduler(sgb_server *sv)
                 std::lock_guard<std::mutex> lk(sv->mu);
                 sv->budget_used -= sh->footprint;
                 sv->done[sh->ticket] = sh;
+                sv->live.erase(sh->ticket);
                 sv->cv_done.notify_all();
                 continue;
             }
@@ -356,12 +362,19 @@ void scheduler(sgb_server *sv)
             for (Shot *sh : sv->resident) {
                 sh->n0 += R * S;
                 if (rc != SGB_OK || e != cudaSuccess) sh->status = SGB_ERR_CUDA;
-                if (sh->n0 > sh->nt || sh->status != SGB_OK) finished.push_back(sh);
+                if (sh->n0 > sh->nt || sh->status != SGB_OK || sh->cancel) finished.push_back(sh);
                 else keep.push_back(sh);
             }
         }
+        for (Shot *sh : joined) {  // cancelled while being set up: never runs
+            if (sh->cancel) {
+                cudaStreamSynchronize(sv->setup_stream);
+                finished.push_back(sh);
+            } else {
+                keep.push_back(sh);
+            }
+        }
         for (Shot *sh : finished) retire_shot(sv, sh);
-        for (Shot *sh : joined) keep.push_back(sh);
         if (!finished.empty() || !joined.empty()) sv->composition_changed = true;
         t_retire = ms_between(tp, Clock::now());
         {
@@ -379,7 +392,9 @@ void scheduler(sgb_server *sv)
             for (Shot *sh : finished) {
                 sv->budget_used -= sh->footprint;
                 sv->done[sh->ticket] = sh;
-                sv->stats.completed += 1;
+                sv->live.erase(sh->ticket);
+                if (sh->status == SGB_ERR_CANCELLED) sv->stats.cancelled += 1;
+                else sv->stats.completed += 1;
             }
             sv->stats.device_bytes = sv->budget_used;
             if (!finished.empty()) sv->cv_done.notify_all();
@@ -502,6 +517,7 @@ extern "C" int serve_submit(sgb_server *sv, const sgb_shot_request *req, uint64_
         }
         sh->ticket = sv->next_ticket++;
         sv->known[sh->ticket] = true;
+        sv->live[sh->ticket] = sh;
         sv->queue.push_back(sh);
         sv->stats.submitted += 1;
         sv->stats.queued = (int)sv->queue.size();
@@ -539,6 +555,30 @@ extern "C" int serve_poll(sgb_server *sv, uint64_t ticket, sgb_shot_result *out,
     return SGB_OK;
 }
 
+extern "C" int serve_cancel(sgb_server *sv, uint64_t ticket)
+{
+    if (!sv) return fail(SGB_ERR_INVALID_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (!sv->known.count(ticket))
+        return fail(SGB_ERR_INVALID_ARG, "serve: unknown ticket %llu", (unsigned long long)ticket);
+    if (sv->done.count(ticket)) return SGB_OK;  // finished already: its result stands
+    Shot *sh = sv->live[ticket];
+    auto it = std::find(sv->queue.begin(), sv->queue.end(), sh);
+    if (it != sv->queue.end()) {  // never admitted: done at once
+        sv->queue.erase(it);
+        sh->status = SGB_ERR_CANCELLED;
+        sh->t_admit = sh->t_done = Clock::now();
+        sv->done[ticket] = sh;
+        sv->live.erase(ticket);
+        sv->stats.cancelled += 1;
+        sv->stats.queued = (int)sv->queue.size();
+        sv->cv_done.notify_all();
+        return SGB_OK;
+    }
+    sh->cancel = true;  // admitted: retired at the end of the current replays
+    return SGB_OK;
+}
+
 extern "C" int serve_stats(sgb_server *sv, sgb_serve_stats *out)
 {
     if (!sv || !out) return fail(SGB_ERR_INVALID_ARG, "NULL argument");
@@ -555,6 +595,7 @@ extern "C" int serve_destroy(sgb_server *sv)
         sv->stop = true;
         for (Shot *sh : sv->queue) {  // cancel what was never admitted
             sh->status = SGB_ERR_REJECTED;
+            sv->live.erase(sh->ticket);
             delete sh;
         }
         sv->queue.clear();

@@ -102,7 +102,8 @@ struct StepArgs {
     float inv_vol;         // 1 / (dx dy dz)
     const int *step_ptr;   // device step counter (graph replays) or null
     int step_add;          // n = *step_ptr + step_add
-    int nrec;              // receivers sampled from u^n into row n - 1 (n >= 1)
+    int nrec;              // receivers sampled from u^n into row n - 1 - rec_n0 (n > rec_n0)
+    int rec_n0;            // first step of the traces buffer (a shot segment's first step)
     const long long *rec_off;
     float *traces;
     ScaleState *scale;     // fp16 storage only
@@ -983,11 +984,11 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     }
 
     // Receivers of the previous step: u^n is read-only in this launch.
-    if (a.nrec > 0 && n >= 1) {
+    if (a.nrec > 0 && n >= 1 + a.rec_n0) {
         const T *uc = static_cast<const T *>(S::OUTV ? u_cur_v : a.u_cur);
         for (int r = unit * C::BLOCK + tid; r < a.nrec; r += units * C::BLOCK) {
             const float v = Elem<T>::get(uc + a.rec_off[r]) * st.s_cur;
-            a.traces[(long long)(n - 1) * a.nrec + r] = v;
+            a.traces[(long long)(n - 1 - a.rec_n0) * a.nrec + r] = v;
             if (!isfinite(v)) atomicOr(a.err, DEV_ERR_NONFINITE);
         }
     }

@@ -25,6 +25,7 @@ ERR_CUDA = -4
 ERR_TIMEOUT = -5
 ERR_NONFINITE = -6
 ERR_REJECTED = -7
+ERR_CANCELLED = -8
 
 FP32 = 0
 FP16_SCALED = 1
@@ -98,7 +99,8 @@ class ServeStats(ctypes.Structure):
                 ("queued", ctypes.c_int32), ("graph_replays", ctypes.c_uint64),
                 ("step_launches", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("setup_ms", ctypes.c_double), ("prepare_ms", ctypes.c_double),
-                ("retire_ms", ctypes.c_double), ("wait_ms", ctypes.c_double)]
+                ("retire_ms", ctypes.c_double), ("wait_ms", ctypes.c_double),
+                ("cancelled", ctypes.c_uint64)]
 
 
 _lib = None
@@ -123,6 +125,11 @@ SIGNATURES = {
     "run_shot": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "run_shot_segment": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "adjoint_shot": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
@@ -144,6 +151,9 @@ SIGNATURES = {
     "serve_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ShotResult),
                                   ctypes.c_int32]),
     "serve_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServeStats)]),
+    "serve_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "sgb_debug_fail_allocations": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64]),
+    "sgb_pool_used_bytes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "serve_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sgb_device_status": (ctypes.c_int, [ctypes.c_void_p]),
     "sgb_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
@@ -321,6 +331,26 @@ def run_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, traces, fina
                           _buf(final_u, "final_u", "float32", N, optional=True), _stream(stream)))
 
 
+def run_shot_segment(g: Grid, velocity, wavelet, n_begin: int, n_end: int, src_ijk, rec_ijk,
+                     traces, u_cur, u_prev, phi, stream=None):
+    """Steps n_begin .. n_end-1 of a shot from the state (u_cur = u^{n_begin},
+    u_prev = u^{n_begin-1}, phi; float32 arrays of the grid's shape, host or
+    device), which is overwritten with the state at n_end; traces receives
+    n_end - n_begin rows."""
+    s = None if src_ijk is None else np.ascontiguousarray(np.asarray(src_ijk, dtype=np.int32))
+    r = np.ascontiguousarray(np.asarray(rec_ijk, dtype=np.int32).reshape(-1, 3))
+    nrec = r.shape[0]
+    N, nb_, ne_ = _points(g), int(n_begin), int(n_end)
+    _check(lib().run_shot_segment(ctypes.byref(g), _buf(velocity, "velocity", "float32", N),
+                                  _buf(wavelet, "wavelet", "float32", ne_, optional=s is None),
+                                  nb_, ne_, None if s is None else s.ctypes.data,
+                                  r.ctypes.data if nrec else None, nrec,
+                                  _buf(traces, "traces", "float32", (ne_ - nb_) * nrec)
+                                  if nrec else None,
+                                  _buf(u_cur, "u_cur", "float32", N), _buf(u_prev, "u_prev", "float32", N),
+                                  _buf(phi, "phi", "float32", N), _stream(stream)))
+
+
 def adjoint_shot(g: Grid, velocity, wavelet, nt: int, src_ijk, rec_ijk, observed, grad_velocity,
                  ckpt_every: int = 0, stream=None) -> float:
     """Trace misfit J = 1/2 sum (d - observed)^2 and, into grad_velocity (fp64,
@@ -383,6 +413,20 @@ def selftest_wait_timeout(limit_us: int, stream=None) -> int:
     return int(st.value)
 
 
+def debug_fail_allocations(after: int, count: int = 1):
+    """Test hook: the library's pool allocations numbered after .. after +
+    count - 1 (counted from this call) fail with ERR_OUT_OF_MEMORY; count 0
+    disarms.  Process-wide."""
+    _check(lib().sgb_debug_fail_allocations(int(after), int(count)))
+
+
+def pool_used_bytes() -> int:
+    """Bytes currently allocated from the current device's library pool."""
+    out = ctypes.c_int64()
+    _check(lib().sgb_pool_used_bytes(ctypes.byref(out)))
+    return int(out.value)
+
+
 def launch_count(reset: bool = False) -> int:
     return int(lib().sgb_launch_count(1 if reset else 0))
 
@@ -429,6 +473,9 @@ class Server:
             return rc, None, None
         _check(rc)
         return rc, res, tr
+
+    def cancel(self, ticket: int):
+        _check(lib().serve_cancel(self.h, int(ticket)))
 
     def stats(self) -> ServeStats:
         out = ServeStats()

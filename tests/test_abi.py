@@ -252,3 +252,35 @@ def test_step2_argument_checks_without_gpu(lib):
     assert L.stencil_step2(ctypes.byref(g16), *fld, 0, None, None) == seisgb.ERR_INVALID_ARG
     g2 = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1.0, 3000)
     assert L.stencil_step2(ctypes.byref(g2), *fld, 0, None, None) == seisgb.ERR_UNSTABLE_DT
+
+
+def test_segment_argument_checks_without_gpu(lib):
+    """run_shot_segment validates before any GPU work: 0 <= n_begin <= n_end,
+    three state arrays, no fp16-scaled storage, no overlap of the state with
+    the inputs."""
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
+    L = seisgb.lib()
+    N = int(np.prod(g.shape))
+    v = np.full(g.shape, 2000, np.float32)
+    w = np.zeros(10, np.float32)
+    src = np.array([5, 5, 5], np.int32)
+    st = [np.zeros(N, np.float32) for _ in range(3)]
+    f = lambda gg, a, b, s0, s1, s2, vel=v: L.run_shot_segment(
+        ctypes.byref(gg), vel.ctypes.data, w.ctypes.data, a, b, src.ctypes.data, None, 0, None,
+        s0, s1, s2, None)
+    p = [x.ctypes.data for x in st]
+    assert f(g, 5, 4, *p) == seisgb.ERR_INVALID_ARG
+    assert f(g, -1, 4, *p) == seisgb.ERR_INVALID_ARG
+    assert f(g, 0, 4, p[0], None, p[2]) == seisgb.ERR_INVALID_ARG
+    assert f(g, 0, 4, p[0], p[0], p[2]) == seisgb.ERR_INVALID_ARG  # state arrays overlap
+    assert "overlaps" in seisgb.last_error()
+    assert f(g, 0, 4, v.ctypes.data, p[1], p[2]) == seisgb.ERR_INVALID_ARG  # state over velocity
+    g16 = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=seisgb.FP16_SCALED)
+    assert f(g16, 0, 4, *p) == seisgb.ERR_INVALID_ARG
+    assert "segments need SGB_FP32 or SGB_BF16" in seisgb.last_error()
+
+
+def test_fault_hook_arguments(lib):
+    assert lib.sgb_debug_fail_allocations(-1, 1) == seisgb.ERR_INVALID_ARG
+    assert lib.sgb_debug_fail_allocations(0, -1) == seisgb.ERR_INVALID_ARG
+    assert lib.sgb_debug_fail_allocations(3, 0) == seisgb.OK  # disarmed
