@@ -101,16 +101,20 @@ def _serve(a):
         dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, vmax)))
         g = seisgb.make_grid(r["nx"], r["ny"], r["nz"], r["nb"], r["h"], r["h"], r["h"], dt, vmax)
         work.append((g, r, synth.ricker(r["nt"], dt, r["fp"])))
-    with seisgb.Server(96 << 30, max_slots=16, steps_per_graph=16) as sv:
+    with seisgb.Server(96 << 30, max_slots=a.slots, steps_per_graph=a.spg) as sv:
         t0 = time.perf_counter()
         tk = [sv.submit(g, r["velocity"], wav, r["nt"], r["src"], r["rec"]) for g, r, wav in work]
         for t, (g, r, wav) in zip(tk, work):
             sv.poll(t, r["nt"], r["rec"].shape[0], timeout_us=600_000_000)
         wall = time.perf_counter() - t0
         st = sv.stats()
-    print(json.dumps({"requests": len(work), "shots_per_s": len(work) / wall, "wall_s": wall,
+    import os
+    print(json.dumps({"requests": len(work), "slots": a.slots, "steps_per_graph": a.spg,
+                      "connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
+                      "shots_per_s": len(work) / wall, "wall_s": wall,
                       "graph_replays": int(st.graph_replays), "wait_ms": st.wait_ms,
-                      "setup_ms": st.setup_ms}))
+                      "setup_ms": st.setup_ms, "prepare_ms": st.prepare_ms,
+                      "retire_ms": st.retire_ms}))
 
 
 def _shots(a):
@@ -205,7 +209,9 @@ def main(argv=None):
     p.add_argument("--storage", choices=["fp16", "bf16"], default=None,
                    help="time a short run_shot with 16-bit wavefield storage")
     p.add_argument("--serve", type=int, default=0,
-                   help="submit this many requests of the serving mix to a 16-slot server")
+                   help="submit this many requests of the serving mix to a server at once")
+    p.add_argument("--slots", type=int, default=16, help="server slots (--serve)")
+    p.add_argument("--spg", type=int, default=16, help="steps per graph replay (--serve)")
     p.add_argument("--shots", action="store_true",
                    help="time whole run_shot calls (layered model) with each time-loop schedule")
     p.add_argument("--step2", action="store_true",
