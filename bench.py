@@ -562,11 +562,15 @@ def main():
     h_tr = torch.zeros((w.nt, nrec), dtype=torch.float32).pin_memory()
     seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
     barrier()
+    clocks_e2e = ClockSampler(uuid)
+    clocks_e2e.start()
+    time.sleep(0.3)
     t = time.perf_counter()
     for _ in range(a.steps):
         seisgb.run_shot(g, h_v, h_w, w.nt, src, rec, h_tr)
     barrier()
     e2e_s = replicas.max_over_ranks(time.perf_counter() - t, device=dev)
+    clk_e2e = clocks_e2e.stop()
     e2e_val = replicas.job_rate(w.points * w.nt * a.steps, e2e_s, world) / 1e9
     h2d = vel.nbytes + wav.nbytes + rec.nbytes + 12
     d2h = w.nt * nrec * 4
@@ -650,7 +654,8 @@ def main():
                      "alg_bytes_per_launch": alg, "peak_source": peak_kind,
                      "step_ms_in_shot": ms_per_step / w.nt},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s / a.steps * 1e3,
+                "clocks": clk_e2e},
         "gpu_launches": launches,
         "clocks": clk,
         "precision": precision,
