@@ -259,10 +259,15 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
             return rc;
     // [k & 1]: reads w^{k+1} = wbuf[(k+1)&1] and mu^{k+1}, writes wbuf[k&1]
     StepMaps amaps[2];
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2; ++p) {
         if ((rc = encode_step_maps<float>(amaps[p], wbuf[(p + 1) & 1], wbuf[p & 1], m,
                                           mbuf[(p + 1) & 1], L)))
             return rc;
+        // mu^{k+1} as a box with its x-y neighbours (x halo 4, y halo 1)
+        using GA = Stage<CfgAdj, float, MODE_ADJ>;
+        if ((rc = encode_map<float>(&amaps[p].phi, mbuf[(p + 1) & 1], L, GA::MBW, GA::MBH, SGB_L2PROMO)))
+            return rc;
+    }
     CUtensorMap gs_map;
     if ((rc = encode_map<float>(&gs_map, gsum, L, CfgAdj::BX, CfgAdj::BY))) return rc;
     StepArgs abase = base;

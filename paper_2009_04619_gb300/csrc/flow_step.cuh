@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     S st;
     st.su = smem_raw;
     st.sp = smem_raw + NU * G::U_BYTES;
-    st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES);
+    st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES + G::MZ_BYTES);
     st.empty_u = st.full_u + NU;
     st.full_p = st.empty_u + NU;
     st.empty_p = st.full_p + NP;

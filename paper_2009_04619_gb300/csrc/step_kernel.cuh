@@ -284,10 +284,18 @@ struct Stage {
     static constexpr int SW = C::BX + 2 * HX;      // u^n box width (elements)
     static constexpr int U_BYTES = align128(SW * C::SH * (int)sizeof(T));
     static constexpr int UP_BYTES = align128(C::P_TILE * (int)sizeof(T));
-    static constexpr int F_BYTES = C::P_TILE * 4;  // one fp32 tile (m, phi / mu, g, S)
-    static constexpr int P_BYTES = UP_BYTES + (MODE == MODE_ADJ ? 4 : 2) * F_BYTES;
+    static constexpr int F_BYTES = C::P_TILE * 4;  // one fp32 tile (m, phi, g, S)
+    // the adjoint's mu^{k+1} tile carries its x-y neighbours: a (BX + 8) x (BY + 2)
+    // box (x halo 4 for the TMA's 16-byte alignment, y halo 1)
+    static constexpr int MBW = C::BX + 8, MBH = C::BY + 2;
+    static constexpr int MU_BYTES = align128(MBW * MBH * 4);
+    static constexpr int PH_BYTES = MODE == MODE_ADJ ? MU_BYTES : F_BYTES;  // phi or mu slot
+    static constexpr int P_BYTES = UP_BYTES + F_BYTES + PH_BYTES + (MODE == MODE_ADJ ? 2 : 0) * F_BYTES;
+    // MODE_ADJ: mu^{k+1} one plane below each thread's points, kept from plane to
+    // plane in shared memory (registers are at their limit)
+    static constexpr int MZ_BYTES = MODE == MODE_ADJ ? C::THREADS * C::TY * 16 : 0;
     static constexpr size_t SMEM_BYTES = size_t(C::NU) * U_BYTES + size_t(C::NP) * P_BYTES +
-                                         size_t(C::NU + C::NP) * 16 +
+                                         size_t(MZ_BYTES) + size_t(C::NU + C::NP) * 16 +
                                          size_t(C::NU + C::NP + 1) * 4;
     static_assert(U_BYTES % 128 == 0 && F_BYTES % 128 == 0, "stage alignment");
     static_assert(SW <= 256, "TMA box limit");
@@ -382,6 +390,14 @@ struct StepCta {
     int phi_xmask;  // phi blocks holding x-PML columns, when the tile touches only the
                     // x-PML (planes outside the z-PML load only these); 0 otherwise
     int phoff;      // offset of this thread's row-0 quad in the blocked phi tile
+    int mbox;           // MODE_ADJ: offset of this thread's row-0 quad in the mu box
+
+    // MODE_ADJ: mu^{k+1} at this thread's row-r points one plane below, kept from
+    // plane to plane in shared memory (registers are at their limit)
+    __device__ __forceinline__ float4 *mz_prev(int r) const
+    {
+        return reinterpret_cast<float4 *>(sp + NP * G::P_BYTES) + r * THREADS + tid;
+    }
     int useq, pseq;  // FLOW: u and (u^{n-1}, m, phi) planes of earlier units of this CTA
     void *u_out_v;   // FLOW, PARITY: the output buffer of the current step
     float s_cur, s_prev, inv_s_next;  // fp16 scales (1 otherwise)
@@ -492,22 +508,26 @@ struct StepCta {
         const int phmask = !pml ? 0 : (phi_xmask && !zpml) ? phi_xmask : (1 << C::PHI_NB) - 1;
         const int ntiles = 1 + (MODE == MODE_ADJ ? 2 : 0);
         constexpr int PHB_BYTES = C::PHI_BW * C::BY * 4;
-        mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + ntiles * G::F_BYTES +
-                                              __popc(phmask) * PHB_BYTES);
+        const int ph_bytes = MODE == MODE_ADJ ? (pml ? G::MBW * G::MBH * 4 : 0)
+                                              : __popc(phmask) * PHB_BYTES;
+        mbar_arrive_expect_tx(full_p + s, P_TILE * (int)sizeof(T) + ntiles * G::F_BYTES + ph_bytes);
         unsigned char *d = sp + s * G::P_BYTES;
         // No evict-first hint: u^{n-1} and phi are overwritten in place (u^{n+1},
         // phi^{n+1}) a few planes later, and marking their lines first-to-go cost
         // 8% of the step at 512^3 (118 MB more DRAM read per launch).
         tma_load_3d(d, tm_uprev, full_p + s, x0, y0, k);
         tma_load_3d(d + G::UP_BYTES, tm_m, full_p + s, x0, y0, k);
+        if constexpr (MODE == MODE_ADJ) {
+            // mu^{k+1} with its x-y halo; g^{k-1} of the recomputation; partial sum S
+            if (pml) tma_load_3d(d + G::UP_BYTES + G::F_BYTES, tm_phi, full_p + s, x0 - 4, y0 - 1, k);
+            tma_load_3d(d + G::UP_BYTES + G::F_BYTES + G::PH_BYTES, tm_acc, full_p + s, x0, y0, k);
+            tma_load_3d(d + G::UP_BYTES + 2 * G::F_BYTES + G::PH_BYTES, tm_gs, full_p + s, x0, y0, k);
+        } else {
 #pragma unroll
-        for (int b = 0; b < C::PHI_NB; ++b)
-            if ((phmask >> b) & 1)
-                tma_load_3d(d + G::UP_BYTES + G::F_BYTES + b * PHB_BYTES, tm_phi, full_p + s,
-                            x0 + b * C::PHI_BW, y0, k);
-        if constexpr (MODE == MODE_ADJ) {  // g^{k-1} of the recomputation; partial sum S
-            tma_load_3d(d + G::UP_BYTES + 2 * G::F_BYTES, tm_acc, full_p + s, x0, y0, k);
-            tma_load_3d(d + G::UP_BYTES + 3 * G::F_BYTES, tm_gs, full_p + s, x0, y0, k);
+            for (int b = 0; b < C::PHI_NB; ++b)
+                if ((phmask >> b) & 1)
+                    tma_load_3d(d + G::UP_BYTES + G::F_BYTES + b * PHB_BYTES, tm_phi, full_p + s,
+                                x0 + b * C::PHI_BW, y0, k);
         }
     }
 
@@ -569,8 +589,9 @@ struct StepCta {
         const T *pup = reinterpret_cast<const T *>(pu);
         const float *pm = reinterpret_cast<const float *>(pu + G::UP_BYTES);
         const float *pph = reinterpret_cast<const float *>(pu + G::UP_BYTES + G::F_BYTES);
-        const float *pg = reinterpret_cast<const float *>(pu + G::UP_BYTES + 2 * G::F_BYTES);
-        const float *pgs = reinterpret_cast<const float *>(pu + G::UP_BYTES + 3 * G::F_BYTES);
+        const float *pg = reinterpret_cast<const float *>(pu + G::UP_BYTES + G::F_BYTES + G::PH_BYTES);
+        const float *pgs =
+            reinterpret_cast<const float *>(pu + G::UP_BYTES + 2 * G::F_BYTES + G::PH_BYTES);
 
         // 25-point Laplacian (Eq. 3): centre and z part from the queue
         float4 L[TY], gy[TY];
@@ -642,7 +663,8 @@ struct StepCta {
             int ptmask = 0;
             float4 ph = make_float4(0.f, 0.f, 0.f, 0.f);
             if (PML) {
-                ph = lds128(pph + phoff + r * C::PHI_BW);
+                if constexpr (MODE == MODE_ADJ) ph = lds128(pph + mbox + r * G::MBW);
+                else ph = lds128(pph + phoff + r * C::PHI_BW);
                 phn = ph;
                 const float eyz = ZP ? __fadd_rn(pey[r], ez) : 0.0f;
                 const float gyk = pgy[r];
@@ -650,19 +672,19 @@ struct StepCta {
                 const int rowmask = (ZP || zin || ((pmy >> r) & 1)) ? 0xF : pmx;
                 const float4 zp = q[r][O + 5], zm = q[r][O + 3];
                 // adjoint: psi = sum_a k_a [G_a mu](x + e_a) - [G_a mu](x - e_a) from the six
-                // neighbours of mu^{k+1} (zero outside the PML and in the halo)
+                // neighbours of mu^{k+1} (zero outside the PML and in the halo): x and y
+                // from the haloed box, -z kept from the plane below, +z from global memory
                 float4 myp = make_float4(0.f, 0.f, 0.f, 0.f), mym = myp, mzp = myp, mzm = myp;
                 float mxl = 0.f, mxr = 0.f;
                 if constexpr (MODE == MODE_ADJ) {
-                    if (store_ok && j < a.Ny) {
-                        const float *mc = a.mu_in + off0 + (long long)r * a.sx;
-                        myp = ldg128(mc + a.sx);
-                        mym = ldg128(mc - a.sx);
-                        mzp = ldg128(mc + a.sxy);
-                        mzm = ldg128(mc - a.sxy);
-                        mxl = __ldg(mc - 1);
-                        mxr = __ldg(mc + 4);
-                    }
+                    const float *mb = pph + mbox + r * G::MBW;
+                    myp = lds128(mb + G::MBW);
+                    mym = lds128(mb - G::MBW);
+                    mxl = mb[-1];
+                    mxr = mb[4];
+                    mzm = *mz_prev(r);
+                    if (store_ok && j < a.Ny) mzp = ldg128(a.mu_in + off0 + (long long)r * a.sx + a.sxy);
+                    *mz_prev(r) = ph;
                 }
                 const float mux[6] = {mxl, ph.x, ph.y, ph.z, ph.w, mxr};
 #pragma unroll
@@ -710,6 +732,7 @@ struct StepCta {
                     }
                 }
             }
+            if constexpr (MODE == MODE_ADJ && !PML) *mz_prev(r) = make_float4(0.f, 0.f, 0.f, 0.f);
             float4 acc4 = Lr;  // MODE_FWD_ACC: g = L u^n + phi^n + f^n
             if constexpr (MODE == MODE_FWD_ACC) {
 #pragma unroll
@@ -804,6 +827,7 @@ struct StepCta {
         store_ok = gi < a.Nx;
         base_off = a.origin + (long long)gj0 * a.sx + gi;
         pml_tables();
+        if constexpr (MODE == MODE_ADJ) mbox = (1 + TY * tyi) * G::MBW + 4 + 4 * txi;
     }
 
     // Prime the register queue with planes z0-4 .. z0+3 and run the unit's
@@ -816,6 +840,14 @@ struct StepCta {
         const StepArgs &a = *pa;
         const int nit = z1 - z0;
         const int u0 = FLOW ? useq : 0;
+        if constexpr (MODE == MODE_ADJ) {  // mu^{k+1} one plane below the unit
+#pragma unroll
+            for (int r = 0; r < TY; ++r)
+                *mz_prev(r) = store_ok && gj0 + r < a.Ny
+                                 ? ldg128(a.mu_in + base_off + (long long)(z0 - 1) * a.sxy +
+                                          (long long)r * a.sx)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             wait(full_u + (u0 + s) % NU, ((u0 + s) / NU) & 1);
@@ -931,7 +963,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     st.tm_gs = tm.gs;
     st.su = smem_raw;
     st.sp = smem_raw + NU * G::U_BYTES;
-    st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES);
+    st.full_u = reinterpret_cast<uint64_t *>(st.sp + NP * G::P_BYTES + G::MZ_BYTES);
     st.empty_u = st.full_u + NU;
     st.full_p = st.empty_u + NU;
     st.empty_p = st.full_p + NP;
