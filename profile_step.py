@@ -68,7 +68,7 @@ def _adjoint(a):
 def _storage(a):
     n_in = a.n - 2 * a.nb
     v = 3000.0
-    fmt = {"fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
+    fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
     g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, 1.0, v)
     dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, v)))
     g = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, dt, v, storage=fmt)
@@ -86,7 +86,8 @@ def _storage(a):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.nt
     pts = a.n ** 3
-    alg = 10 * pts + 8 * (pts - n_in ** 3)  # 2 B wavefields (3 x), 4 B m, phi at PML points
+    # wavefields read twice and written once, 4 B m, phi read and written at PML points
+    alg = (3 * (4 if a.storage == "fp32" else 2) + 4) * pts + 8 * (pts - n_in ** 3)
     print(json.dumps({"n": a.n, "nb": a.nb, "storage": a.storage, "nt": a.nt, "ms_per_step": ms,
                       "gpts": pts / ms / 1e6, "alg_gbs": alg / ms / 1e6}))
 
@@ -134,7 +135,7 @@ def _shots(a):
     out = {"n": a.n, "nb": a.nb, "nt": a.nt}
     scheds = {"step": seisgb.SCHED_STEP, "flow": seisgb.SCHED_FLOW}
     if a.storage:
-        fmt = {"fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
+        fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
     else:
         fmt = seisgb.FP32
     for name, sched in scheds.items():
@@ -206,7 +207,7 @@ def main(argv=None):
     p.add_argument("--adjoint", action="store_true", help="time one misfit-gradient shot")
     p.add_argument("--nt", type=int, default=200, help="time steps of the gradient shot")
     p.add_argument("--ckpt", type=int, default=100, help="checkpoint interval of the gradient shot")
-    p.add_argument("--storage", choices=["fp16", "bf16"], default=None,
+    p.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default=None,
                    help="time a short run_shot with 16-bit wavefield storage")
     p.add_argument("--serve", type=int, default=0,
                    help="submit this many requests of the serving mix to a server at once")
