@@ -289,9 +289,9 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
             a.step_add = n;
             a.acc_out = seg + (size_t)(n - na) * L.elems;
             const StepMaps &mp = fmaps[n & 1];
-            fwd_acc_kernel<Cfg><<<grid, Cfg::BLOCK, Stage<Cfg, float, MODE_FWD_ACC>::SMEM_BYTES, st>>>(
-                a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi);
-            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(launch_dependent(fwd_acc_kernel<Cfg>, grid, Cfg::BLOCK,
+                                      Stage<Cfg, float, MODE_FWD_ACC>::SMEM_BYTES, st, a, mp.ucur,
+                                      mp.ucur_in, mp.uprev, mp.m, mp.phi));
             ++t_launches;
         }
         for (int k = nbnd; k >= na + 1; --k) {  // adjoint steps
@@ -302,10 +302,10 @@ extern "C" int adjoint_shot(const sgb_grid *g, const float *velocity, const floa
             a.mu_in = mbuf[(k + 1) & 1];
             a.step_add = k;
             const StepMaps &mp = amaps[k & 1];
-            adjoint_step_kernel<CfgAdj><<<agrid, CfgAdj::BLOCK,
-                                          Stage<CfgAdj, float, MODE_ADJ>::SMEM_BYTES, st>>>(
-                a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi, acc_maps[k - 1 - na], gs_map);
-            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(launch_dependent(adjoint_step_kernel<CfgAdj>, agrid, CfgAdj::BLOCK,
+                                      Stage<CfgAdj, float, MODE_ADJ>::SMEM_BYTES, st, a, mp.ucur,
+                                      mp.ucur_in, mp.uprev, mp.m, mp.phi, acc_maps[k - 1 - na],
+                                      gs_map));
             inject_residual_kernel<<<(nrec + 255) / 256, 256, 0, st>>>(
                 wbuf[k & 1], m, seg + (size_t)(k - 1 - na) * L.elems, gsum, d_off, nrec,
                 d_tr + (size_t)(k - 1) * nrec, d_obs + (size_t)(k - 1) * nrec);

@@ -121,6 +121,17 @@ __device__ __forceinline__ float4 lds128(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
+// Programmatic dependent launch. Blocks until the grids this launch depends on
+// have completed and their writes are visible (a no-op after a plain launch),
+// then lets the next launch of the stream place its CTAs in this grid's tail,
+// where they wait here in turn. A kernel launched with the programmatic
+// serialisation attribute calls this before its first global access.
+__device__ __forceinline__ void grid_dependency_sync()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Streaming 128-bit global store (written once, not re-read by this kernel).
 __device__ __forceinline__ void stg128(float *p, float4 v)
 {

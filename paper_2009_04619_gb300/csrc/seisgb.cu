@@ -51,6 +51,37 @@ static int fail(int code, const char *fmt, ...)
                         __LINE__);                                                       \
     } while (0)
 
+// Launch of a step kernel (one that calls grid_dependency_sync first). Issued
+// directly on a stream, it allows programmatic stream serialisation: its CTAs
+// may be placed while the previous kernel of the stream drains, so launch
+// latency and CTA set-up overlap that kernel's last wave (measured 2-5% per
+// step at 192^3-256^3, 2% on the adjoint's step loop). Inside a stream capture
+// it is a plain launch: graph replays already launch back to back, and there
+// the early CTAs cost up to 3% at 128^3.
+#ifndef SGB_PDL
+#define SGB_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), int grid, int block, size_t smem,
+                             cudaStream_t st, Args... args)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed =
+        SGB_PDL && cap == cudaStreamCaptureStatusNone ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 extern "C" const char *sgb_last_error(void) { return t_last_error.c_str(); }
 
 extern "C" int64_t sgb_launch_count(int reset)
@@ -331,9 +362,8 @@ int encode_step_maps(StepMaps &mp, const void *u_cur, const void *u_prev, const 
 template <class T>
 int launch_step(const StepArgs &a, const StepMaps &mp, int grid, cudaStream_t st)
 {
-    fused_step_kernel<Cfg, T><<<grid, Cfg::BLOCK, Stage<Cfg, T>::SMEM_BYTES, st>>>(
-        a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi);
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(launch_dependent(fused_step_kernel<Cfg, T>, grid, Cfg::BLOCK, Stage<Cfg, T>::SMEM_BYTES,
+                              st, a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi));
     ++t_launches;
     return SGB_OK;
 }
@@ -858,9 +888,9 @@ int launch_pair(const sgb_grid *g, const PairPlan &pp, const PairMaps &pm, const
         a.step_ptr = step_ptr;
         a.step_add = step_add + h;
         const StepMaps &mp = h == 0 ? pm.shell0 : pm.shell1;
-        shell_step_kernel<Cfg><<<nunits, Cfg::BLOCK, Stage<Cfg, float>::SMEM_BYTES, st>>>(
-            a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi);
-        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(launch_dependent(shell_step_kernel<Cfg>, nunits, Cfg::BLOCK,
+                                  Stage<Cfg, float>::SMEM_BYTES, st, a, mp.ucur, mp.ucur_in,
+                                  mp.uprev, mp.m, mp.phi));
         ++t_launches;
     }
     (void)g;

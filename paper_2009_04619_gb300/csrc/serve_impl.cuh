@@ -258,10 +258,10 @@ int prepare_replay(sgb_server *sv)
                 r.step_ptr = sh->d_step;
                 r.step_add = k;
                 r.n_end = sh->nt;
-                shot_step_kernel<Cfg><<<sh->grid, Cfg::BLOCK, Stage<Cfg, float>::SMEM_BYTES, bs>>>(
-                    sh->args, r, p0.ucur, p0.ucur_in, p0.uprev, p0.m, p0.phi, p1.ucur, p1.ucur_in,
-                    p1.uprev, p1.m, p1.phi);
-                ce = cudaGetLastError();
+                ce = launch_dependent(shot_step_kernel<Cfg>, sh->grid, Cfg::BLOCK,
+                                      Stage<Cfg, float>::SMEM_BYTES, bs, sh->args, r, p0.ucur,
+                                      p0.ucur_in, p0.uprev, p0.m, p0.phi, p1.ucur, p1.ucur_in,
+                                      p1.uprev, p1.m, p1.phi);
             }
             if (ce == cudaSuccess) {
                 advance_kernel<<<1, 32, 0, bs>>>(sh->d_step, S);

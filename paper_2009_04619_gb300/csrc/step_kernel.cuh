@@ -1073,6 +1073,7 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
                       const __grid_constant__ CUtensorMap tm_m,
                       const __grid_constant__ CUtensorMap tm_phi)
 {
+    grid_dependency_sync();
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     step_unit<C, T>(a, tm, blockIdx.x, gridDim.x, n, false);
@@ -1088,6 +1089,7 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
                       const __grid_constant__ CUtensorMap tm_m,
                       const __grid_constant__ CUtensorMap tm_phi)
 {
+    grid_dependency_sync();
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     step_unit<C, float, MODE_FWD, VAR_SHELL>(a, tm, blockIdx.x, gridDim.x, n, false);
@@ -1119,6 +1121,7 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
                      const __grid_constant__ CUtensorMap m1_m,
                      const __grid_constant__ CUtensorMap m1_phi)
 {
+    grid_dependency_sync();
     const int n = *r.step_ptr + r.step_add;
     if (n > r.n_end) return;  // finished: waits for retirement
     const bool odd = n & 1;
@@ -1139,6 +1142,7 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
                    const __grid_constant__ CUtensorMap tm_m,
                    const __grid_constant__ CUtensorMap tm_phi)
 {
+    grid_dependency_sync();
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     step_unit<C, float, MODE_FWD_ACC>(a, tm, blockIdx.x, gridDim.x, a.step_add, false);
 }
@@ -1158,6 +1162,7 @@ __global__ void __launch_bounds__(C::BLOCK, C::MINB)
                         const __grid_constant__ CUtensorMap tm_acc,
                         const __grid_constant__ CUtensorMap tm_gs)
 {
+    grid_dependency_sync();
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_mu, &tm_acc, &tm_gs};
     step_unit<C, float, MODE_ADJ>(a, tm, blockIdx.x, gridDim.x, a.step_add, false);
 }
