@@ -41,10 +41,16 @@ extern "C" {
 #define SGB_ERR_REJECTED (-7)
 #define SGB_ERR_CANCELLED (-8)
 
-/* Wavefield storage formats (arithmetic is always fp32). */
+/* Wavefield storage formats (arithmetic is always fp32).  The _DIFF formats
+ * keep the leapfrog state of Eq. 2 as (u^n, d^n = u^n - u^{n-1}) instead of
+ * (u^n, u^{n-1}): the same scheme in exact arithmetic, but a rounding error
+ * stored in u^n no longer also enters the time difference, so 16-bit storage
+ * loses far less accuracy.  They take a third wavefield (run_shot only). */
 #define SGB_FP32 0
 #define SGB_FP16_SCALED 1
 #define SGB_BF16 2
+#define SGB_FP32_DIFF 3
+#define SGB_BF16_DIFF 4
 
 /* Problem statement (section III-B: inner-region size and PML width are
  * inputs; Eq. 2: spacing and dt). */
@@ -58,15 +64,15 @@ typedef struct {
                             the model's maximum velocity */
     float pml_r0;        /* PML target reflection coefficient in (0, 1];
                             1 switches the damping off */
-    int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED or SGB_BF16 */
+    int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED, SGB_BF16, SGB_FP32_DIFF or
+                            SGB_BF16_DIFF (the last two: run_shot only) */
     int32_t schedule;    /* how run_shot launches its time loop (SGB_SCHED_*);
                             every schedule gives the same bits.  Other entry
                             points ignore it. */
 } sgb_grid;
 
 /* run_shot time-loop schedules (the arithmetic per point is the same in all):
- *  SGB_SCHED_AUTO   the library's choice (SGB_SCHED_FLOW, or SGB_SCHED_STEP
- *                   for SGB_FP16_SCALED storage);
+ *  SGB_SCHED_AUTO   the library's choice (SGB_SCHED_STEP, measured fastest);
  *  SGB_SCHED_STEP   one launch per step, replayed in CUDA graphs of 32 steps;
  *  SGB_SCHED_PAIRS  temporal blocking: two steps per pass over HBM on the
  *                   PML-free interior, see stencil_step2 (SGB_FP32 only);

@@ -134,6 +134,8 @@ struct DevState {
     int occ = 0;     // resident CTAs of the fp32 step kernel per SM
     int occ_h = 0;   // ... fp16 storage
     int occ_b = 0;   // ... bf16 storage
+    int occ_df = 0;  // ... difference form, fp32 storage
+    int occ_db = 0;  // ... difference form, bf16 storage
     int *err = nullptr;
     cudaMemPool_t pool = nullptr;
 };
@@ -144,15 +146,21 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 // Allow the step kernel for storage T its dynamic shared memory; report how
 // many of its CTAs fit on one SM.
-template <class T>
+template <class T, bool DIFF = false>
+auto step_kernel_of()
+{
+    if constexpr (DIFF) return diff_step_kernel<Cfg, T>;
+    else return fused_step_kernel<Cfg, T>;
+}
+
+template <class T, bool DIFF = false>
 int prepare_step_kernel(int *occ)
 {
     using G = Stage<Cfg, T>;
-    CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel<Cfg, T>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const auto kern = step_kernel_of<T, DIFF>();
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)G::SMEM_BYTES));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fused_step_kernel<Cfg, T>,
-                                                           Cfg::BLOCK, G::SMEM_BYTES));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, Cfg::BLOCK, G::SMEM_BYTES));
     if (*occ < 1) return fail(SGB_ERR_CUDA, "step kernel does not fit on an SM");
     return SGB_OK;
 }
@@ -170,6 +178,8 @@ int device_state(DevState **out)
         if ((rc0 = prepare_step_kernel<float>(&s.occ))) return rc0;
         if ((rc0 = prepare_step_kernel<__half>(&s.occ_h))) return rc0;
         if ((rc0 = prepare_step_kernel<__nv_bfloat16>(&s.occ_b))) return rc0;
+        if ((rc0 = prepare_step_kernel<float, true>(&s.occ_df))) return rc0;
+        if ((rc0 = prepare_step_kernel<__nv_bfloat16, true>(&s.occ_db))) return rc0;
         CUDA_TRY(cudaGetSymbolAddress((void **)&s.err, g_dev_err));
         cudaMemPoolProps props;
         memset(&props, 0, sizeof props);
@@ -232,13 +242,13 @@ int check_grid(const sgb_grid *g, sgb_layout_info *L)
     if (!finite_pos(g->vmax)) return fail(SGB_ERR_INVALID_ARG, "vmax must be finite and > 0");
     if (!(g->pml_r0 > 0.0f && g->pml_r0 <= 1.0f))
         return fail(SGB_ERR_INVALID_ARG, "pml_r0 must be in (0, 1] (got %g)", (double)g->pml_r0);
-    if (g->storage != SGB_FP32 && g->storage != SGB_FP16_SCALED && g->storage != SGB_BF16)
+    if (g->storage < SGB_FP32 || g->storage > SGB_BF16_DIFF)
         return fail(SGB_ERR_INVALID_ARG, "unknown storage format %d", g->storage);
     if (g->schedule < SGB_SCHED_AUTO || g->schedule > SGB_SCHED_FLOW)
         return fail(SGB_ERR_INVALID_ARG, "unknown schedule %d", g->schedule);
     if (g->schedule == SGB_SCHED_PAIRS && g->storage != SGB_FP32)
         return fail(SGB_ERR_INVALID_ARG, "SGB_SCHED_PAIRS needs SGB_FP32 storage");
-    if (g->schedule == SGB_SCHED_FLOW && g->storage == SGB_FP16_SCALED)
+    if (g->schedule == SGB_SCHED_FLOW && g->storage != SGB_FP32 && g->storage != SGB_BF16)
         return fail(SGB_ERR_INVALID_ARG, "SGB_SCHED_FLOW needs SGB_FP32 or SGB_BF16 storage");
     compute_layout(g, L);
     if (L->elems > (int64_t(1) << 40)) return fail(SGB_ERR_INVALID_ARG, "field too large");
@@ -359,10 +369,10 @@ int encode_step_maps(StepMaps &mp, const void *u_cur, const void *u_prev, const 
     return SGB_OK;
 }
 
-template <class T>
+template <class T, bool DIFF = false>
 int launch_step(const StepArgs &a, const StepMaps &mp, int grid, cudaStream_t st)
 {
-    CUDA_TRY(launch_dependent(fused_step_kernel<Cfg, T>, grid, Cfg::BLOCK, Stage<Cfg, T>::SMEM_BYTES,
+    CUDA_TRY(launch_dependent(step_kernel_of<T, DIFF>(), grid, Cfg::BLOCK, Stage<Cfg, T>::SMEM_BYTES,
                               st, a, mp.ucur, mp.ucur_in, mp.uprev, mp.m, mp.phi));
     ++t_launches;
     return SGB_OK;
@@ -661,6 +671,9 @@ int stencil_step_common(const sgb_grid *g, const void *u_cur, void *u_prev_to_ne
     sgb_layout_info L;
     int rc = check_grid(g, &L);
     if (rc) return rc;
+    if (g->storage == SGB_FP32_DIFF || g->storage == SGB_BF16_DIFF)
+        return fail(SGB_ERR_INVALID_ARG,
+                    "stencil_step: the difference-form storage keeps a third field (run_shot only)");
     if (!u_cur || !u_prev_to_next || !m) return fail(SGB_ERR_INVALID_ARG, "NULL field pointer");
     if (g->nb > 0 && !phi) return fail(SGB_ERR_INVALID_ARG, "phi is required when nb > 0");
     if (!aligned16(u_cur) || !aligned16(u_prev_to_next) || !aligned16(m) || (phi && !aligned16(phi)) ||
@@ -995,7 +1008,7 @@ int run_flow(const sgb_layout_info &L, DevState *ds, cudaStream_t st, Scratch &s
 
 // Shot time loop and outputs for wavefield storage T (run_shot after its
 // argument checks and the CFL check).
-template <class T>
+template <class T, bool DIFF = false>
 // Steps n_begin .. n_end-1; state: null (start from zero fields) or three
 // device compact fp32 arrays (u^n, u^{n-1}, phi^n) read at n_begin and
 // overwritten with the state at n_end.  Traces rows are steps n_begin ...
@@ -1012,10 +1025,15 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     float *phi, *m;
     ScaleState *ss = nullptr;
     int *d_step;
+    void *dfield = nullptr;  // difference form: d^n = u^n - u^{n-1}, updated in place
     if ((rc = sc.get(&u0, ubytes)) || (rc = sc.get(&u1, ubytes)) ||
         (rc = sc.get((void **)&phi, fbytes)) || (rc = sc.get((void **)&m, fbytes)) ||
         (rc = sc.get((void **)&d_step, sizeof(int))))
         return rc;
+    if (DIFF) {
+        if ((rc = sc.get(&dfield, ubytes))) return rc;
+        CUDA_TRY(cudaMemsetAsync(dfield, 0, ubytes, st));
+    }
     CUDA_TRY(cudaMemcpyAsync(d_step, &n_begin, sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemsetAsync(m, 0, fbytes, st));
     if (!state) {
@@ -1062,13 +1080,17 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     base.rec_off = d_off;
     base.traces = d_tr;
     base.rec_n0 = n_begin;
-    const int occ = std::is_same<T, float>::value ? ds->occ
+    base.d_io = dfield;
+    const int occ = DIFF ? (std::is_same<T, float>::value ? ds->occ_df : ds->occ_db)
+                    : std::is_same<T, float>::value ? ds->occ
                     : std::is_same<T, __half>::value ? ds->occ_h : ds->occ_b;
     int grid = 0;
     choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, occ, base, &grid);
-    StepMaps maps[2];  // [parity of n]
+    StepMaps maps[2];  // [parity of n]; the difference form reads d^n through the u^{n-1} map
     for (int p = 0; p < 2; ++p)
-        if ((rc = encode_step_maps<T>(maps[p], buf[(p + 1) & 1], buf[p & 1], m, phi, L))) return rc;
+        if ((rc = encode_step_maps<T>(maps[p], buf[(p + 1) & 1], DIFF ? dfield : buf[p & 1], m, phi,
+                                      L)))
+            return rc;
 
     auto args_for = [&](int parity, const int *step_ptr, int step_add) {
         StepArgs a = base;
@@ -1080,7 +1102,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     };
 
     bool looped = false;
-    if constexpr (!Elem<T>::SCALED) {
+    if constexpr (!Elem<T>::SCALED && !DIFF) {
         if (resolve_schedule(g) == SGB_SCHED_FLOW && nsteps > 0) {
             if ((rc = run_flow<T>(L, ds, st, sc, base, maps, buf, n_begin, n_end, rec_ijk, nrec)))
                 return rc;
@@ -1098,7 +1120,8 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
             for (int i = 0; i < GS && crc == SGB_OK; ++i)
-                crc = launch_step<T>(args_for(n_begin + i, d_step, i), maps[(n_begin + i) & 1], grid, cs);
+                crc = launch_step<T, DIFF>(args_for(n_begin + i, d_step, i), maps[(n_begin + i) & 1],
+                                           grid, cs);
             if (crc == SGB_OK) {
                 advance_kernel<<<1, 32, 0, cs>>>(d_step, GS);
                 ce = cudaGetLastError();
@@ -1121,7 +1144,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         CUDA_TRY(ce);
     }
     for (int n = looped ? n_end : n_begin + replays * GS; n < n_end; ++n)
-        if ((rc = launch_step<T>(args_for(n, nullptr, n), maps[n & 1], grid, st))) return rc;
+        if ((rc = launch_step<T, DIFF>(args_for(n, nullptr, n), maps[n & 1], grid, st))) return rc;
 
     // u^k lives in buf[(k+1)&1] (written by step k-1): u^{nt} in buf[(nt+1)&1]
     const void *u_final_dev = buf[(nt + 1) & 1];
@@ -1370,7 +1393,7 @@ int run_shot_common(const sgb_grid *g, const float *velocity, const float *wavel
     if (nrec < 0) return fail(SGB_ERR_INVALID_ARG, "nrec < 0");
     if (nrec > 0 && (!rec_ijk || (nsteps > 0 && !traces)))
         return fail(SGB_ERR_INVALID_ARG, "receiver arrays NULL");
-    if (state && g->storage == SGB_FP16_SCALED)
+    if (state && g->storage != SGB_FP32 && g->storage != SGB_BF16)
         return fail(SGB_ERR_INVALID_ARG, "shot segments need SGB_FP32 or SGB_BF16 storage");
     if (src_ijk && !in_inner(g, src_ijk[0], src_ijk[1], src_ijk[2]))
         return fail(SGB_ERR_INVALID_ARG, "source (%d,%d,%d) outside the inner region", src_ijk[0],
@@ -1467,6 +1490,15 @@ int run_shot_common(const sgb_grid *g, const float *velocity, const float *wavel
     case SGB_BF16:
         rc = run_shot_t<__nv_bfloat16>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end, src_ijk,
                                        rec_ijk, nrec, d_off, d_tr, final_u, dst, d_err);
+        break;
+    case SGB_FP32_DIFF:
+        rc = run_shot_t<float, true>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end, src_ijk,
+                                     rec_ijk, nrec, d_off, d_tr, final_u, dst, d_err);
+        break;
+    case SGB_BF16_DIFF:
+        rc = run_shot_t<__nv_bfloat16, true>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end,
+                                             src_ijk, rec_ijk, nrec, d_off, d_tr, final_u, dst,
+                                             d_err);
         break;
     default:
         // temporal blocking covers whole shots; a segment takes one step per launch

@@ -72,7 +72,13 @@ enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_RANGE = 4 };
 // Kernel modes: the forward step; the forward step that also stores its
 // acceleration term g^n = L u^n + phi^n + f^n (recomputation for the adjoint);
 // the adjoint step (see adjoint notes below).
-enum : int { MODE_FWD = 0, MODE_FWD_ACC = 1, MODE_ADJ = 2 };
+// MODE_DIFF: the forward step in difference form. The state is (u^n, d^n) with
+// d^n = u^n - u^{n-1} instead of (u^n, u^{n-1}): the same scheme in exact
+// arithmetic, but a rounding error stored in u no longer also enters the time
+// difference, so stored 16-bit values lose far less (each field keeps its own
+// relative precision). d is read through the u^{n-1} tile map and updated in
+// place through d_io; u^{n+1} goes to u_out.
+enum : int { MODE_FWD = 0, MODE_FWD_ACC = 1, MODE_ADJ = 2, MODE_DIFF = 3 };
 
 // Plane kinds of a work unit (compile-time paths of the plane body).
 enum : int { PLANE_INTERIOR = 0, PLANE_XY = 1, PLANE_Z = 2 };
@@ -86,6 +92,7 @@ struct ScaleState {
 
 struct StepArgs {
     void *u_out;           // padded base: holds u^{n-1} on entry, u^{n+1} on exit
+    void *d_io;            // MODE_DIFF: padded base of d^n on entry, d^{n+1} on exit
     const void *u_cur;     // padded base of u^n (receiver pre-sampling only)
     float *phi;            // padded base of phi (PML auxiliary field, fp32)
     int Nx, Ny, Nz;        // computed extents
@@ -652,11 +659,18 @@ struct StepCta {
                 c = f4mul(s_cur, c);
                 up = f4mul(s_prev, up);
             }
-            float4 un;
-            un.x = fmaf(mm.x, Lr.x, fmaf(2.0f, c.x, -up.x));
-            un.y = fmaf(mm.y, Lr.y, fmaf(2.0f, c.y, -up.y));
-            un.z = fmaf(mm.z, Lr.z, fmaf(2.0f, c.z, -up.z));
-            un.w = fmaf(mm.w, Lr.w, fmaf(2.0f, c.w, -up.w));
+            float4 un;  // MODE_DIFF: d^{n+1} until the source is added
+            if constexpr (MODE == MODE_DIFF) {  // up = d^n: d^{n+1} = d^n + m L u^n
+                un.x = fmaf(mm.x, Lr.x, up.x);
+                un.y = fmaf(mm.y, Lr.y, up.y);
+                un.z = fmaf(mm.z, Lr.z, up.z);
+                un.w = fmaf(mm.w, Lr.w, up.w);
+            } else {
+                un.x = fmaf(mm.x, Lr.x, fmaf(2.0f, c.x, -up.x));
+                un.y = fmaf(mm.y, Lr.y, fmaf(2.0f, c.y, -up.y));
+                un.z = fmaf(mm.z, Lr.z, fmaf(2.0f, c.z, -up.z));
+                un.w = fmaf(mm.w, Lr.w, fmaf(2.0f, c.w, -up.w));
+            }
             const int j = gj0 + r;
             float4 phn = make_float4(0.f, 0.f, 0.f, 0.f);
             bool any_pml = false;
@@ -714,11 +728,19 @@ struct StepCta {
                         rhs = fmaf(-hzm, f4get(mzm, e), rhs);
                     }
                     const float lr = __fadd_rn(f4get(Lr, e), rhs);
-                    // [(2 - e^2) c - (1 - e) u^{n-1} + m lr] / (1 + e)
-                    //   = (1 - e) c + [c - (1 - e) u^{n-1} + m lr] / (1 + e)
-                    const float upml =
-                        fmaf(inv, fmaf(f4get(mm, e), lr, fmaf(-ome, f4get(up, e), cc)),
-                             __fmul_rn(ome, cc));
+                    float upml;
+                    if constexpr (MODE == MODE_DIFF) {
+                        // d^{n+1} = u^{n+1} - c with u^{n-1} = c - d^n:
+                        //   [(1 - e) d^n + m lr - e^2 c] / (1 + e)
+                        const float ed = __fsub_rn(1.0f, ome);
+                        upml = __fmul_rn(inv, fmaf(f4get(mm, e), lr,
+                                                   fmaf(ome, f4get(up, e), -__fmul_rn(__fmul_rn(ed, ed), cc))));
+                    } else {
+                        // [(2 - e^2) c - (1 - e) u^{n-1} + m lr] / (1 + e)
+                        //   = (1 - e) c + [c - (1 - e) u^{n-1} + m lr] / (1 + e)
+                        upml = fmaf(inv, fmaf(f4get(mm, e), lr, fmaf(-ome, f4get(up, e), cc)),
+                                    __fmul_rn(ome, cc));
+                    }
                     const float ppml = __fmul_rn(__fsub_rn(pe, Gd), inv);
                     ptmask |= int(pt) << e;
                     if constexpr (MODE == MODE_ADJ) {
@@ -746,6 +768,12 @@ struct StepCta {
                 f4set(un, e, fmaf(f4get(mm, e), f, f4get(un, e)));
                 if constexpr (MODE == MODE_FWD_ACC) f4set(acc4, e, f4get(acc4, e) + f);
             }
+            float4 dn;  // MODE_DIFF: d^{n+1}; u^{n+1} = u^n + d^{n+1}
+            if constexpr (MODE == MODE_DIFF) {
+                dn = un;
+                un = make_float4(__fadd_rn(c.x, dn.x), __fadd_rn(c.y, dn.y), __fadd_rn(c.z, dn.z),
+                                 __fadd_rn(c.w, dn.w));
+            }
             // shell launches leave the box to the two-step kernel (its x bounds
             // are multiples of 4: a quad is wholly inside or outside)
             const bool boxed = SHELL && gi >= a.bx0 && gi < a.bx1 && j >= a.by0 && j < a.by1 &&
@@ -759,13 +787,21 @@ struct StepCta {
                 }
                 T *uo = static_cast<T *>(OUTV ? u_out_v : a.u_out) + off;
                 const bool wphi = PML && any_pml;  // phi^{n+1}, or mu^k in the adjoint
+                // MODE_DIFF: d^{n+1} rounded with its own random word (an odd
+                // multiple of u's, so uniform and distinct)
+                T *dio = nullptr;
+                if constexpr (MODE == MODE_DIFF) dio = static_cast<T *>(a.d_io) + off;
+                const uint32_t rnd_d = rnd * 0x2C1B3C6Du;
                 if (gi + 3 < a.Nx) {
                     E::st(uo, un, rnd);
+                    if constexpr (MODE == MODE_DIFF) E::st(dio, dn, rnd_d);
                     if (wphi) stg128(a.phi + off, phn);
                     if constexpr (MODE == MODE_FWD_ACC) stg128(a.acc_out + off, acc4);
                 } else {
                     for (int e = 0; e < 4 && gi + e < a.Nx; ++e) {
                         E::put(uo + e, f4get(un, e), hash_bits(rnd, (uint32_t)e));
+                        if constexpr (MODE == MODE_DIFF)
+                            E::put(dio + e, f4get(dn, e), hash_bits(rnd_d, (uint32_t)e));
                         if (wphi) a.phi[off + e] = f4get(phn, e);
                         if constexpr (MODE == MODE_FWD_ACC) a.acc_out[off + e] = f4get(acc4, e);
                     }
@@ -947,7 +983,8 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     using S = StepCta<C, T, MODE, VAR>;
     constexpr bool SHELL = VAR == VAR_SHELL;
     using G = Stage<C, T, MODE>;
-    static_assert(MODE == MODE_FWD || sizeof(T) == 4, "the adjoint runs in fp32");
+    static_assert(MODE == MODE_FWD || MODE == MODE_DIFF || sizeof(T) == 4,
+                  "the adjoint runs in fp32");
     constexpr int TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
     constexpr int BX = C::BX, BY = C::BY;
 
@@ -1077,6 +1114,22 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_uprev, &tm_m, &tm_phi, nullptr, nullptr};
     const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
     step_unit<C, T>(a, tm, blockIdx.x, gridDim.x, n, false);
+}
+
+// One time step in difference form (MODE_DIFF): one CTA per work unit.
+template <class C, class T>
+__global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
+    diff_step_kernel(const __grid_constant__ StepArgs a,
+                     const __grid_constant__ CUtensorMap tm_ucur,
+                     const __grid_constant__ CUtensorMap tm_ucur_in,
+                     const __grid_constant__ CUtensorMap tm_d,
+                     const __grid_constant__ CUtensorMap tm_m,
+                     const __grid_constant__ CUtensorMap tm_phi)
+{
+    grid_dependency_sync();
+    const StepMapPtrs tm = {&tm_ucur, &tm_ucur_in, &tm_d, &tm_m, &tm_phi, nullptr, nullptr};
+    const int n = (a.step_ptr ? *a.step_ptr : 0) + a.step_add;
+    step_unit<C, T, MODE_DIFF>(a, tm, blockIdx.x, gridDim.x, n, false);
 }
 
 // One fused step on the work units of a table, storing nothing inside the

@@ -30,6 +30,10 @@ ERR_CANCELLED = -8
 FP32 = 0
 FP16_SCALED = 1
 BF16 = 2
+# difference form: the state (u^n, u^n - u^{n-1}) instead of (u^n, u^{n-1});
+# a third wavefield, run_shot only
+FP32_DIFF = 3
+BF16_DIFF = 4
 
 # run_shot time-loop schedules (sgb_grid.schedule)
 SCHED_AUTO = 0

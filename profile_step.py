@@ -68,7 +68,8 @@ def _adjoint(a):
 def _storage(a):
     n_in = a.n - 2 * a.nb
     v = 3000.0
-    fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
+    fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16,
+           "fp32_diff": seisgb.FP32_DIFF, "bf16_diff": seisgb.BF16_DIFF}[a.storage]
     g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, 1.0, v)
     dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, v)))
     g = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, dt, v, storage=fmt)
@@ -86,8 +87,11 @@ def _storage(a):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.nt
     pts = a.n ** 3
-    # wavefields read twice and written once, 4 B m, phi read and written at PML points
-    alg = (3 * (4 if a.storage == "fp32" else 2) + 4) * pts + 8 * (pts - n_in ** 3)
+    # wavefields read twice and written once (difference form: u^n and d^n read,
+    # u^{n+1} and d^{n+1} written), 4 B m, phi read and written at PML points
+    wb = 4 if a.storage.startswith("fp32") else 2
+    nw = 4 if a.storage.endswith("_diff") else 3
+    alg = (nw * wb + 4) * pts + 8 * (pts - n_in ** 3)
     print(json.dumps({"n": a.n, "nb": a.nb, "storage": a.storage, "nt": a.nt, "ms_per_step": ms,
                       "gpts": pts / ms / 1e6, "alg_gbs": alg / ms / 1e6}))
 
@@ -135,7 +139,8 @@ def _shots(a):
     out = {"n": a.n, "nb": a.nb, "nt": a.nt}
     scheds = {"step": seisgb.SCHED_STEP, "flow": seisgb.SCHED_FLOW}
     if a.storage:
-        fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16}[a.storage]
+        fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16,
+           "fp32_diff": seisgb.FP32_DIFF, "bf16_diff": seisgb.BF16_DIFF}[a.storage]
     else:
         fmt = seisgb.FP32
     for name, sched in scheds.items():
@@ -207,7 +212,7 @@ def main(argv=None):
     p.add_argument("--adjoint", action="store_true", help="time one misfit-gradient shot")
     p.add_argument("--nt", type=int, default=200, help="time steps of the gradient shot")
     p.add_argument("--ckpt", type=int, default=100, help="checkpoint interval of the gradient shot")
-    p.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default=None,
+    p.add_argument("--storage", choices=["fp32", "fp16", "bf16", "fp32_diff", "bf16_diff"], default=None,
                    help="time a short run_shot with 16-bit wavefield storage")
     p.add_argument("--serve", type=int, default=0,
                    help="submit this many requests of the serving mix to a server at once")

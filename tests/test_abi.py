@@ -233,6 +233,44 @@ def test_schedules_check_storage(lib):
     seisgb.layout(g)
 
 
+def test_difference_form_storage_checks(lib):
+    """The difference-form formats run through run_shot with one launch per
+    step: the other schedules, stencil_step, segments, the allocation-free
+    entry point and the server reject them before any GPU work; unknown
+    storage codes are rejected."""
+    L = seisgb.lib()
+    for storage in (seisgb.FP32_DIFF, seisgb.BF16_DIFF):
+        for sched in (seisgb.SCHED_AUTO, seisgb.SCHED_STEP):
+            seisgb.layout(seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=storage,
+                                           schedule=sched))
+        for sched in (seisgb.SCHED_PAIRS, seisgb.SCHED_FLOW):
+            g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=storage, schedule=sched)
+            with pytest.raises(seisgb.SeisgbError) as e:
+                seisgb.layout(g)
+            assert e.value.code == seisgb.ERR_INVALID_ARG and "SCHED" in str(e.value)
+        g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=storage)
+        E = int(seisgb.layout(g).elems)
+        buf = np.zeros(5 * E + 16, np.float32)
+        b = buf.ctypes.data + (16 - buf.ctypes.data % 16) % 16
+        fld = [b + 4 * E * q for q in range(4)]
+        assert L.stencil_step(ctypes.byref(g), fld[0], fld[1], fld[2], fld[3], 0, None, None,
+                              None) == seisgb.ERR_INVALID_ARG
+        assert "difference-form" in seisgb.last_error()
+        N = int(np.prod(g.shape))
+        v = np.full(g.shape, 2000, np.float32)
+        w = np.zeros(10, np.float32)
+        src = np.array([5, 5, 5], np.int32)
+        st = [np.zeros(N, np.float32) for _ in range(3)]
+        assert L.run_shot_segment(ctypes.byref(g), v.ctypes.data, w.ctypes.data, 0, 4,
+                                  src.ctypes.data, None, 0, None, *[x.ctypes.data for x in st],
+                                  None) == seisgb.ERR_INVALID_ARG
+        assert "segments need SGB_FP32 or SGB_BF16" in seisgb.last_error()
+    for bad in (-1, 5):
+        g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=bad)
+        with pytest.raises(seisgb.SeisgbError):
+            seisgb.layout(g)
+
+
 def test_step2_argument_checks_without_gpu(lib):
     """stencil_step2 validates before any GPU work: four distinct aligned
     buffers, fp32 storage, phi with a PML, the CFL limit."""

@@ -1,5 +1,6 @@
-"""16-bit wavefield storage (fp16 with a per-field power-of-two scale, bf16)
-with fp32 arithmetic: error against the fp64 oracle, stated per format."""
+"""16-bit wavefield storage (fp16 with a per-field power-of-two scale, bf16,
+and the difference-form state u^n, u^n - u^{n-1}) with fp32 arithmetic: error
+against the fp64 oracle, stated per format."""
 import numpy as np
 import pytest
 import torch
@@ -62,6 +63,62 @@ def test_small_case_error_per_format():
     assert errs["fp16"][0] < errs["bf16"][0]
 
 
+def test_difference_form_small_case():
+    """The difference-form formats (state u^n, d^n = u^n - u^{n-1}) on the small
+    case, 64^3 + PML 16, 100 steps, receivers on the source plane.  In fp32 the
+    form is the same scheme as the leapfrog up to rounding, so it meets the
+    fp32 bound (2e-5) against the oracle, PML included (measured 2.7e-6 /
+    5.2e-7).  In bf16 a stored rounding error of u no longer enters the time
+    difference: measured 1.0e-2 / 5.4e-3 against 2.4e-2 / 1.1e-2 for the bf16
+    leapfrog state; the bounds are about 3x the measured errors."""
+    ensure_lib()
+    w = synth.SMALL
+    vel = w.velocity()
+    rec = _source_plane_receivers(w)
+    errs = {}
+    ref = None
+    for name, fmt in (("fp32_diff", seisgb.FP32_DIFF), ("bf16_diff", seisgb.BF16_DIFF),
+                      ("bf16", seisgb.BF16)):
+        tr, u, dt, wav, rec = _run(w, vel, fmt, w.nt, rec)
+        if ref is None:
+            ref = _oracle(w, vel, dt, wav, rec, w.nt)
+        assert np.abs(tr).max() > 0
+        errs[name] = (rel_l2(u, ref["u"]), rel_l2(tr, ref["traces"]))
+    print("difference form, small case rel L2 (wavefield, traces):", errs)
+    assert errs["fp32_diff"][0] <= 2e-5 and errs["fp32_diff"][1] <= 2e-5
+    assert errs["bf16_diff"][0] <= 3e-2 and errs["bf16_diff"][1] <= 1.6e-2
+    assert errs["bf16_diff"][0] < 0.7 * errs["bf16"][0]
+
+
+def test_fp32_difference_form_ragged_layered_vs_oracle():
+    """FP32_DIFF on a ragged anisotropic layered grid (several tiles, PML 7,
+    source near a PML corner, receivers spread over the depth) against the fp64
+    oracle: the fp32 bound of the leapfrog path (2e-5 relative L2)."""
+    ensure_lib()
+    nx, ny, nz, nb, nt = 101, 45, 38, 7, 90
+    shape = (nz + 2 * nb, ny + 2 * nb, nx + 2 * nb)
+    vel = synth.layered_model(shape, seed=33, sigma=2.0)
+    vmax = float(vel.max())
+    h = (10.0, 12.0, 9.0)
+    dt = float(np.float32(0.4 * oracle.cfl_dt(vmax, *h)))
+    wav = synth.ricker(nt, dt, 25.0)
+    src = (nb + 3, nb + ny - 4, nb + 5)
+    rng = np.random.default_rng(5)
+    rec = synth.surface_receivers(nx, ny, nb, 5)
+    rec[:, 2] = nb + rng.integers(0, nz, rec.shape[0])
+    rec = rec.astype(np.int32)
+    g = seisgb.make_grid(nx, ny, nz, nb, *h, dt, vmax, storage=seisgb.FP32_DIFF)
+    tr = torch.zeros((nt, rec.shape[0]), dtype=torch.float32, device="cuda")
+    u = torch.zeros(g.shape, dtype=torch.float32, device="cuda")
+    seisgb.run_shot(g, torch.from_numpy(vel).cuda(), torch.from_numpy(wav).cuda(), nt, src, rec,
+                    tr, u)
+    go = oracle.Grid(nx, ny, nz, nb, *h, dt, vmax=vmax, r0=float(np.float32(1e-3)))
+    ref = oracle.run_shot(go, vel, wav, nt, src, rec)
+    assert np.abs(ref["traces"]).max() > 0
+    assert rel_l2(u.cpu().numpy(), ref["u"]) <= 2e-5
+    assert rel_l2(tr.cpu().numpy(), ref["traces"]) <= 2e-5
+
+
 @pytest.mark.slow
 def test_256_cube_1000_steps_error_per_format():
     """The reduced-precision error check on the layered model at 256^3 computed
@@ -69,13 +126,16 @@ def test_256_cube_1000_steps_error_per_format():
     when written (wavefield, traces): fp32 1.8e-4 / 9.9e-5, fp16 2.2e-2 / 1.3e-2,
     bf16 1.8e-1 / 1.1e-1 (stochastic rounding; with round-to-nearest fp16 was
     1.4e-1 / 6.9e-2 and bf16 diverged).  fp32 error grows with the step count:
-    2.7e-6 after 100 steps of the small case, 1.8e-4 after 1000 here."""
+    2.7e-6 after 100 steps of the small case, 1.8e-4 after 1000 here.  The
+    difference form brings bf16 below 1e-1: measured 5.1e-2 / 2.6e-2
+    (BF16_DIFF), and 1.1e-4 / 2.8e-5 for FP32_DIFF."""
     ensure_lib()
     w = synth.scaled(synth.LARGE, 192, 32, 1000, name="fwd256_pml32_layered_ricker10_nt1000")
     vel = w.velocity()
     errs = {}
     ref = None
-    for name, fmt in FORMATS.items():
+    formats = dict(FORMATS, fp32_diff=seisgb.FP32_DIFF, bf16_diff=seisgb.BF16_DIFF)
+    for name, fmt in formats.items():
         tr, u, dt, wav, rec = _run(w, vel, fmt, w.nt)
         if ref is None:
             ref = _oracle(w, vel, dt, wav, rec, w.nt)
@@ -84,6 +144,8 @@ def test_256_cube_1000_steps_error_per_format():
     assert errs["fp32"][0] <= 5e-4 and errs["fp32"][1] <= 5e-4
     assert errs["fp16"][0] <= 5e-2 and errs["fp16"][1] <= 4e-2
     assert errs["bf16"][0] <= 4e-1 and errs["bf16"][1] <= 3e-1
+    assert errs["fp32_diff"][0] <= 5e-4 and errs["fp32_diff"][1] <= 5e-4
+    assert errs["bf16_diff"][0] <= 1e-1 and errs["bf16_diff"][1] <= 8e-2
 
 
 # Stored mantissa bits of the 16-bit formats: fp16 keeps 10, bf16 7.
