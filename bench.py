@@ -275,7 +275,7 @@ def _gradient_alg_bytes(w, nt, ckpt, fold=32):
             + -(-nt // fold) * 24 * N)
 
 
-def _gradient(a, seisgb, synth, peak):
+def _gradient(a, seisgb, synth, peak, uuid=None):
     """Adjoint-gradient leg: 16 shots of the 256^3 / 2000-step workload, misfit
     against traces of the unperturbed model, gradients summed over the shots
     (fp64); shots/s, forward-equivalent Gpt/s and the whole computation's
@@ -324,11 +324,15 @@ def _gradient(a, seisgb, synth, peak):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+    sampler = ClockSampler(uuid) if uuid else None
+    if sampler:
+        sampler.start()
     e0.record(stream)
     J, total = replicas.gradient_sum(shot_fn, len(shots), grads[0], workers=workers,
                                      streams=streams)
     e1.record(stream)
     torch.cuda.synchronize()
+    clk = sampler.stop() if sampler else None
     t = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3, device=grads[0].device)
     tr = torch.zeros((nt, rec.shape[0]), dtype=torch.float32, device="cuda")
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -349,7 +353,7 @@ def _gradient(a, seisgb, synth, peak):
             "gpts_forward_equivalent": w.points * nt * ns / t / 1e9,
             "forward_ms_per_shot": t_fwd * 1e3, "ratio_to_forward": t / ns / t_fwd,
             "alg_bytes_per_shot": alg, "achieved_gbs": gbs, "frac": gbs / peak,
-            "misfit": J, "grad_l2": float(total.norm()),
+            "misfit": J, "grad_l2": float(total.norm()), "clocks": clk,
             "grad_finite": bool(torch.isfinite(total).all()),
             "accuracy": "gradient vs the fp64 oracle adjoint (32^3, 50 steps) and the oracle vs "
                         "central differences: tests"}
@@ -650,7 +654,7 @@ def main():
     small = _small_case(a, seisgb, synth, dev, barrier)
 
     serving = _serving(a, seisgb, synth, value) if a.serve_requests > 0 else None
-    gradient = _gradient(a, seisgb, synth, peak) if a.grad_shots > 0 else None
+    gradient = _gradient(a, seisgb, synth, peak, uuid) if a.grad_shots > 0 else None
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
