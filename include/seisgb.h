@@ -45,7 +45,8 @@ extern "C" {
  * keep the leapfrog state of Eq. 2 as (u^n, d^n = u^n - u^{n-1}) instead of
  * (u^n, u^{n-1}): the same scheme in exact arithmetic, but a rounding error
  * stored in u^n no longer also enters the time difference, so 16-bit storage
- * loses far less accuracy.  They take a third wavefield (run_shot only). */
+ * loses far less accuracy.  They take a third wavefield: run_shot (one launch
+ * per step) and stencil_step_diff. */
 #define SGB_FP32 0
 #define SGB_FP16_SCALED 1
 #define SGB_BF16 2
@@ -65,7 +66,8 @@ typedef struct {
     float pml_r0;        /* PML target reflection coefficient in (0, 1];
                             1 switches the damping off */
     int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED, SGB_BF16, SGB_FP32_DIFF or
-                            SGB_BF16_DIFF (the last two: run_shot only) */
+                            SGB_BF16_DIFF (the last two: run_shot and
+                            stencil_step_diff) */
     int32_t schedule;    /* how run_shot launches its time loop (SGB_SCHED_*);
                             every schedule gives the same bits.  Other entry
                             points ignore it. */
@@ -127,8 +129,9 @@ int sgb_cfl_dt(const sgb_grid *g, float vmax, float *dt_max);
  * fp32 padded layout, read and written at PML points only (start from zeros).
  * The u fields hold g->storage elements in the padded layout: fp32
  * (SGB_FP32) or bf16 (SGB_BF16, stored with stochastic rounding, arithmetic
- * in fp32); SGB_FP16_SCALED fields go through stencil_step_scaled (INVALID_ARG
- * here).  step selects src->wavelet[step].
+ * in fp32); SGB_FP16_SCALED fields go through stencil_step_scaled and the
+ * difference-form formats through stencil_step_diff (INVALID_ARG here).  step
+ * selects src->wavelet[step].
  * src and rec may be NULL.  All device pointers must be 16-byte aligned.
  * Asynchronous on stream.  UNSTABLE_DT when g->dt exceeds the CFL limit for
  * g->vmax.  A bounded kernel wait that gave up or a non-finite receiver sample
@@ -152,6 +155,22 @@ int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_to_next, con
 int stencil_step_scaled(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
                         const float *m, float *phi, float *scale_state, int32_t step,
                         const sgb_source *src, const sgb_receivers *rec, void *stream);
+
+/* One step of Eq. 2 in difference form (g->storage SGB_FP32_DIFF or
+ * SGB_BF16_DIFF, padded fields of fp32 or bf16 elements): the leapfrog state
+ * is u^n and d^n = u^n - u^{n-1}.  Reads u_cur = u^n and d = d^n; writes
+ * d^{n+1} = d^n + m L u^n (PML points: [(1 - e) d^n + m (L u^n + phi^n)
+ * - e^2 u^n] / (1 + e) with e = eta dt; the source term added to d^{n+1}) over
+ * d in place, and u^{n+1} = u^n + d^{n+1} into u_next.  The same scheme as
+ * stencil_step in exact arithmetic; stored 16-bit values lose much less
+ * because a rounding of u no longer enters the time difference.  u_cur,
+ * u_next and d must be distinct, 16-byte aligned device buffers of
+ * sgb_layout().elems elements; m and phi as for stencil_step.  Receivers sample
+ * u^{n+1}.  Returns INVALID_ARG (nothing launched) for other storage formats,
+ * a NULL d, or d equal to u_cur or u_next; otherwise as stencil_step. */
+int stencil_step_diff(const sgb_grid *g, const void *u_cur, void *u_next, void *d,
+                      const float *m, float *phi, int32_t step, const sgb_source *src,
+                      const sgb_receivers *rec, void *stream);
 
 /* Two time steps, n and n + 1, with temporal blocking (the 3.5D blocking
  * that the paper names as future work, section VI): on the box B = the inner

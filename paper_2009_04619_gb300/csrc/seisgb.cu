@@ -612,18 +612,20 @@ extern "C" int sgb_device_status(void *stream)
 
 namespace {
 
-// One step of storage type T on caller-owned fields (stencil_step and
-// stencil_step_scaled after their argument checks).
-template <class T>
+// One step of storage type T on caller-owned fields (stencil_step,
+// stencil_step_scaled and stencil_step_diff after their argument checks). DIFF:
+// the difference form, d_io holding d^n on entry and d^{n+1} on exit.
+template <class T, bool DIFF = false>
 int stencil_step_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaStream_t st,
-                   const void *u_cur, void *u_out, const float *m, float *phi, ScaleState *scale,
-                   int32_t step, const sgb_source *src, const sgb_receivers *rec)
+                   const void *u_cur, void *u_out, void *d_io, const float *m, float *phi,
+                   ScaleState *scale, int32_t step, const sgb_source *src, const sgb_receivers *rec)
 {
     int rc;
     StepArgs a;
     fill_step_constants(g, L, a);
     a.u_out = u_out;
     a.u_cur = u_cur;
+    a.d_io = d_io;
     a.phi = phi;
     a.err = ds->err;
     a.step_add = step;
@@ -635,13 +637,14 @@ int stencil_step_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cu
         a.wavelet = src->wavelet;
         a.m_src = m + L.origin + (long long)src->k * L.stride_z + (long long)src->j * L.sx + src->i;
     }
-    const int occ = std::is_same<T, float>::value ? ds->occ
+    const int occ = DIFF ? (std::is_same<T, float>::value ? ds->occ_df : ds->occ_db)
+                    : std::is_same<T, float>::value ? ds->occ
                     : std::is_same<T, __half>::value ? ds->occ_h : ds->occ_b;
     int grid = 0;
     choose_decomposition(L.Nx, L.Ny, L.Nz, ds->sms, occ, a, &grid);
     StepMaps mp;
-    if ((rc = encode_step_maps<T>(mp, a.u_cur, a.u_out, m, phi, L))) return rc;
-    if ((rc = launch_step<T>(a, mp, grid, st))) return rc;
+    if ((rc = encode_step_maps<T>(mp, a.u_cur, DIFF ? d_io : a.u_out, m, phi, L))) return rc;
+    if ((rc = launch_step<T, DIFF>(a, mp, grid, st))) return rc;
     if (rec && rec->nrec > 0) {
         std::vector<long long> off(rec->nrec);
         for (int r = 0; r < rec->nrec; ++r)
@@ -664,16 +667,23 @@ int stencil_step_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cu
     return SGB_OK;
 }
 
-int stencil_step_common(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
+int stencil_step_common(const sgb_grid *g, const void *u_cur, void *u_prev_to_next, void *d_io,
                         const float *m, float *phi, float *scale, int32_t step,
                         const sgb_source *src, const sgb_receivers *rec, void *stream)
 {
     sgb_layout_info L;
     int rc = check_grid(g, &L);
     if (rc) return rc;
-    if (g->storage == SGB_FP32_DIFF || g->storage == SGB_BF16_DIFF)
+    const bool diff = g->storage == SGB_FP32_DIFF || g->storage == SGB_BF16_DIFF;
+    if (diff && !d_io)
         return fail(SGB_ERR_INVALID_ARG,
-                    "stencil_step: the difference-form storage keeps a third field (run_shot only)");
+                    "stencil_step: the difference-form storage keeps a third field; use "
+                    "stencil_step_diff");
+    if (!diff && d_io)
+        return fail(SGB_ERR_INVALID_ARG,
+                    "stencil_step_diff: storage must be SGB_FP32_DIFF or SGB_BF16_DIFF");
+    if (d_io && (!aligned16(d_io) || d_io == u_cur || d_io == u_prev_to_next))
+        return fail(SGB_ERR_INVALID_ARG, "d must be 16-byte aligned and distinct from u_cur, u_next");
     if (!u_cur || !u_prev_to_next || !m) return fail(SGB_ERR_INVALID_ARG, "NULL field pointer");
     if (g->nb > 0 && !phi) return fail(SGB_ERR_INVALID_ARG, "phi is required when nb > 0");
     if (!aligned16(u_cur) || !aligned16(u_prev_to_next) || !aligned16(m) || (phi && !aligned16(phi)) ||
@@ -703,13 +713,20 @@ int stencil_step_common(const sgb_grid *g, const void *u_cur, void *u_prev_to_ne
     ScaleState *ss = reinterpret_cast<ScaleState *>(scale);
     switch (g->storage) {
     case SGB_FP16_SCALED:
-        return stencil_step_t<__half>(g, L, ds, st, u_cur, u_prev_to_next, m, phi, ss, step, src, rec);
+        return stencil_step_t<__half>(g, L, ds, st, u_cur, u_prev_to_next, nullptr, m, phi, ss, step,
+                                      src, rec);
     case SGB_BF16:
-        return stencil_step_t<__nv_bfloat16>(g, L, ds, st, u_cur, u_prev_to_next, m, phi, nullptr,
-                                             step, src, rec);
+        return stencil_step_t<__nv_bfloat16>(g, L, ds, st, u_cur, u_prev_to_next, nullptr, m, phi,
+                                             nullptr, step, src, rec);
+    case SGB_FP32_DIFF:
+        return stencil_step_t<float, true>(g, L, ds, st, u_cur, u_prev_to_next, d_io, m, phi,
+                                           nullptr, step, src, rec);
+    case SGB_BF16_DIFF:
+        return stencil_step_t<__nv_bfloat16, true>(g, L, ds, st, u_cur, u_prev_to_next, d_io, m,
+                                                   phi, nullptr, step, src, rec);
     default:
-        return stencil_step_t<float>(g, L, ds, st, u_cur, u_prev_to_next, m, phi, nullptr, step,
-                                     src, rec);
+        return stencil_step_t<float>(g, L, ds, st, u_cur, u_prev_to_next, nullptr, m, phi, nullptr,
+                                     step, src, rec);
     }
 }
 
@@ -722,7 +739,16 @@ extern "C" int stencil_step(const sgb_grid *g, const void *u_cur, void *u_prev_t
     if (g && g->storage == SGB_FP16_SCALED)
         return fail(SGB_ERR_INVALID_ARG,
                     "stencil_step: SGB_FP16_SCALED fields carry a scale state; use stencil_step_scaled");
-    return stencil_step_common(g, u_cur, u_prev_to_next, m, phi, nullptr, step, src, rec, stream);
+    return stencil_step_common(g, u_cur, u_prev_to_next, nullptr, m, phi, nullptr, step, src, rec,
+                               stream);
+}
+
+extern "C" int stencil_step_diff(const sgb_grid *g, const void *u_cur, void *u_next, void *d,
+                                 const float *m, float *phi, int32_t step, const sgb_source *src,
+                                 const sgb_receivers *rec, void *stream)
+{
+    if (!d) return fail(SGB_ERR_INVALID_ARG, "stencil_step_diff: d is NULL");
+    return stencil_step_common(g, u_cur, u_next, d, m, phi, nullptr, step, src, rec, stream);
 }
 
 extern "C" int stencil_step_scaled(const sgb_grid *g, const void *u_cur, void *u_prev_to_next,
@@ -732,8 +758,8 @@ extern "C" int stencil_step_scaled(const sgb_grid *g, const void *u_cur, void *u
     if (!g || g->storage != SGB_FP16_SCALED)
         return fail(SGB_ERR_INVALID_ARG, "stencil_step_scaled: storage must be SGB_FP16_SCALED");
     if (!scale_state) return fail(SGB_ERR_INVALID_ARG, "stencil_step_scaled: scale_state is NULL");
-    return stencil_step_common(g, u_cur, u_prev_to_next, m, phi, scale_state, step, src, rec,
-                               stream);
+    return stencil_step_common(g, u_cur, u_prev_to_next, nullptr, m, phi, scale_state, step, src,
+                               rec, stream);
 }
 
 namespace {

@@ -31,7 +31,7 @@ FP32 = 0
 FP16_SCALED = 1
 BF16 = 2
 # difference form: the state (u^n, u^n - u^{n-1}) instead of (u^n, u^{n-1});
-# a third wavefield, run_shot only
+# a third wavefield: run_shot and stencil_step_diff
 FP32_DIFF = 3
 BF16_DIFF = 4
 
@@ -118,6 +118,10 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.POINTER(Source), ctypes.POINTER(Receivers),
                                     ctypes.c_void_p]),
+    "stencil_step_diff": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.POINTER(Source),
+                                         ctypes.POINTER(Receivers), ctypes.c_void_p]),
     "stencil_step_scaled": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.POINTER(Source),
@@ -260,7 +264,8 @@ def _stream(stream):
     return stream.cuda_stream
 
 
-_WAVE_DTYPE = {FP32: "float32", FP16_SCALED: "float16", BF16: "bfloat16"}
+_WAVE_DTYPE = {FP32: "float32", FP16_SCALED: "float16", BF16: "bfloat16",
+               FP32_DIFF: "float32", BF16_DIFF: "bfloat16"}
 
 
 def stencil_step(g: Grid, u_cur, u_prev_to_next, m, phi, step: int = 0, source=None,
@@ -297,6 +302,36 @@ def stencil_step(g: Grid, u_cur, u_prev_to_next, m, phi, step: int = 0, source=N
     else:
         rc = lib().stencil_step(ctypes.byref(g), *fields, php, int(step), srcp, recp,
                                 _stream(stream))
+    del keep
+    _check(rc)
+
+
+def stencil_step_diff(g: Grid, u_cur, u_next, d, m, phi, step: int = 0, source=None,
+                      receivers=None, stream=None):
+    """One step in difference form (g.storage FP32_DIFF or BF16_DIFF): reads
+    u_cur = u^n and d = u^n - u^{n-1}, writes u^{n+1} into u_next and d^{n+1}
+    over d.  Fields: CUDA tensors in the padded layout (u_cur, u_next, d of
+    g.storage elements; m, phi float32); source and receivers as for
+    stencil_step."""
+    E = int(layout(g).elems)
+    wdt = _WAVE_DTYPE.get(int(g.storage), "float32")
+    src = None
+    if source is not None:
+        i, j, k, w = source
+        src = Source(int(i), int(j), int(k), _buf(w, "wavelet", "float32", int(step) + 1, cuda=True))
+    rec = None
+    keep = None
+    if receivers is not None:
+        ijk, row = receivers
+        keep = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
+        rec = Receivers(keep.shape[0], keep.ctypes.data,
+                        _buf(row, "traces row", "float32", keep.shape[0], cuda=True))
+    fields = [_buf(u_cur, "u_cur", wdt, E, cuda=True), _buf(u_next, "u_next", wdt, E, cuda=True),
+              _buf(d, "d", wdt, E, cuda=True), _buf(m, "m", "float32", E, cuda=True),
+              _buf(phi, "phi", "float32", E, cuda=True)]
+    rc = lib().stencil_step_diff(ctypes.byref(g), *fields, int(step),
+                                 ctypes.byref(src) if src is not None else None,
+                                 ctypes.byref(rec) if rec is not None else None, _stream(stream))
     del keep
     _check(rc)
 

@@ -235,9 +235,10 @@ def test_schedules_check_storage(lib):
 
 def test_difference_form_storage_checks(lib):
     """The difference-form formats run through run_shot with one launch per
-    step: the other schedules, stencil_step, segments, the allocation-free
-    entry point and the server reject them before any GPU work; unknown
-    storage codes are rejected."""
+    step and through stencil_step_diff: the other schedules, stencil_step,
+    segments, the allocation-free entry point and the server reject them, and
+    stencil_step_diff rejects other formats and aliased or misaligned fields,
+    all before any GPU work; unknown storage codes are rejected."""
     L = seisgb.lib()
     for storage in (seisgb.FP32_DIFF, seisgb.BF16_DIFF):
         for sched in (seisgb.SCHED_AUTO, seisgb.SCHED_STEP):
@@ -255,7 +256,17 @@ def test_difference_form_storage_checks(lib):
         fld = [b + 4 * E * q for q in range(4)]
         assert L.stencil_step(ctypes.byref(g), fld[0], fld[1], fld[2], fld[3], 0, None, None,
                               None) == seisgb.ERR_INVALID_ARG
-        assert "difference-form" in seisgb.last_error()
+        assert "stencil_step_diff" in seisgb.last_error()
+        sd = lambda u, un, d, gg=g: L.stencil_step_diff(ctypes.byref(gg), u, un, d, fld[3], fld[3],
+                                                        0, None, None, None)
+        assert sd(fld[0], fld[1], None) == seisgb.ERR_INVALID_ARG      # no d
+        assert sd(fld[0], fld[1], fld[0]) == seisgb.ERR_INVALID_ARG    # d = u_cur
+        assert sd(fld[0], fld[1], fld[1]) == seisgb.ERR_INVALID_ARG    # d = u_next
+        assert sd(fld[0], fld[0], fld[2]) == seisgb.ERR_INVALID_ARG    # u_next = u_cur
+        assert sd(fld[0], fld[1], fld[2] + 4) == seisgb.ERR_INVALID_ARG  # misaligned d
+        g_plain = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000)
+        assert sd(fld[0], fld[1], fld[2], g_plain) == seisgb.ERR_INVALID_ARG
+        assert "SGB_FP32_DIFF or SGB_BF16_DIFF" in seisgb.last_error()
         N = int(np.prod(g.shape))
         v = np.full(g.shape, 2000, np.float32)
         w = np.zeros(10, np.float32)
