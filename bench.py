@@ -315,9 +315,10 @@ def _gradient(a, seisgb, synth, peak, uuid=None):
         return seisgb.adjoint_shot(g, d_v, d_w, nt, shots[i], rec, obs[i], grads[k], ckpt_every=C,
                                    stream=streams[k]), grads[k]
 
-    if mine:
-        with torch.cuda.stream(streams[0]):
-            shot_fn(mine[0], 0)  # warm-up
+    # warm-up: one shot on every worker at once, so that each worker's scratch
+    # (~16 GB per shot in flight) is allocated and first touched before timing
+    replicas.gradient_sum(shot_fn, min(len(shots), workers * world), grads[0], workers=workers,
+                          streams=streams)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
