@@ -608,10 +608,10 @@ def main():
     del bufs, d_m
 
     # the same shot with 16-bit wavefield storage (fp32 arithmetic); the
-    # difference form (bf16_diff) runs through run_shot only
+    # difference forms (fp16_diff, bf16_diff) are timed inside the shot
     precision = {}
     for fname, fmt in (("fp16_scaled", seisgb.FP16_SCALED), ("bf16", seisgb.BF16),
-                       ("bf16_diff", seisgb.BF16_DIFF)):
+                       ("fp16_diff", seisgb.FP16_DIFF), ("bf16_diff", seisgb.BF16_DIFF)):
         gp = seisgb.make_grid(w.nx, w.ny, w.nz, w.nb, w.h, w.h, w.h, dt, vmax, storage=fmt)
         seisgb.run_shot(gp, d_v, d_w, w.nt, src, rec, d_tr)
         barrier()
@@ -622,7 +622,7 @@ def main():
         p1.record(stream)
         barrier()
         pms = replicas.max_over_ranks(p0.elapsed_time(p1), device=dev) / a.steps
-        diff = fmt == seisgb.BF16_DIFF
+        diff = fmt in (seisgb.BF16_DIFF, seisgb.FP16_DIFF)
         alg16 = _alg_bytes_per_launch(w, wave_bytes=2, wave_fields=4 if diff else 3)
         if diff:  # no single-step entry point: the step time inside the shot
             kms, kname = pms / w.nt, "diff_step_kernel (in run_shot)"
@@ -642,7 +642,9 @@ def main():
                          "alg_bytes_per_launch": alg16},
             "error": "relative L2 vs the fp64 oracle: see the 256^3 x 1000-step precision test"}
         if diff:
-            precision[fname]["state"] = "u^n and d^n = u^n - u^{n-1} in bf16 (difference form)"
+            precision[fname]["state"] = ("u^n and d^n = u^n - u^{n-1} (difference form), "
+                                         + ("fp16 with a scale each" if fmt == seisgb.FP16_DIFF
+                                            else "bf16"))
 
     # temporal blocking: the same shot with SCHED_PAIRS (two steps per HBM
     # pass on the PML-free interior, identical results), and the pair unit

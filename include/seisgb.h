@@ -46,12 +46,15 @@ extern "C" {
  * (u^n, u^{n-1}): the same scheme in exact arithmetic, but a rounding error
  * stored in u^n no longer also enters the time difference, so 16-bit storage
  * loses far less accuracy.  They take a third wavefield: run_shot (one launch
- * per step) and stencil_step_diff. */
+ * per step) and stencil_step_diff.  SGB_FP16_DIFF is the scaled fp16 form
+ * (a power-of-two scale for u and one for d, kept by the library): run_shot
+ * only. */
 #define SGB_FP32 0
 #define SGB_FP16_SCALED 1
 #define SGB_BF16 2
 #define SGB_FP32_DIFF 3
 #define SGB_BF16_DIFF 4
+#define SGB_FP16_DIFF 5
 
 /* Problem statement (section III-B: inner-region size and PML width are
  * inputs; Eq. 2: spacing and dt). */
@@ -65,9 +68,9 @@ typedef struct {
                             the model's maximum velocity */
     float pml_r0;        /* PML target reflection coefficient in (0, 1];
                             1 switches the damping off */
-    int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED, SGB_BF16, SGB_FP32_DIFF or
-                            SGB_BF16_DIFF (the last two: run_shot and
-                            stencil_step_diff) */
+    int32_t storage;     /* SGB_FP32, SGB_FP16_SCALED, SGB_BF16, SGB_FP32_DIFF,
+                            SGB_BF16_DIFF (these two: run_shot and
+                            stencil_step_diff) or SGB_FP16_DIFF (run_shot) */
     int32_t schedule;    /* how run_shot launches its time loop (SGB_SCHED_*);
                             every schedule gives the same bits.  Other entry
                             points ignore it. */

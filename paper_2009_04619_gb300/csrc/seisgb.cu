@@ -136,6 +136,7 @@ struct DevState {
     int occ_b = 0;   // ... bf16 storage
     int occ_df = 0;  // ... difference form, fp32 storage
     int occ_db = 0;  // ... difference form, bf16 storage
+    int occ_dh = 0;  // ... difference form, fp16 storage (scaled)
     int *err = nullptr;
     cudaMemPool_t pool = nullptr;
 };
@@ -180,6 +181,7 @@ int device_state(DevState **out)
         if ((rc0 = prepare_step_kernel<__nv_bfloat16>(&s.occ_b))) return rc0;
         if ((rc0 = prepare_step_kernel<float, true>(&s.occ_df))) return rc0;
         if ((rc0 = prepare_step_kernel<__nv_bfloat16, true>(&s.occ_db))) return rc0;
+        if ((rc0 = prepare_step_kernel<__half, true>(&s.occ_dh))) return rc0;
         CUDA_TRY(cudaGetSymbolAddress((void **)&s.err, g_dev_err));
         cudaMemPoolProps props;
         memset(&props, 0, sizeof props);
@@ -242,7 +244,7 @@ int check_grid(const sgb_grid *g, sgb_layout_info *L)
     if (!finite_pos(g->vmax)) return fail(SGB_ERR_INVALID_ARG, "vmax must be finite and > 0");
     if (!(g->pml_r0 > 0.0f && g->pml_r0 <= 1.0f))
         return fail(SGB_ERR_INVALID_ARG, "pml_r0 must be in (0, 1] (got %g)", (double)g->pml_r0);
-    if (g->storage < SGB_FP32 || g->storage > SGB_BF16_DIFF)
+    if (g->storage < SGB_FP32 || g->storage > SGB_FP16_DIFF)
         return fail(SGB_ERR_INVALID_ARG, "unknown storage format %d", g->storage);
     if (g->schedule < SGB_SCHED_AUTO || g->schedule > SGB_SCHED_FLOW)
         return fail(SGB_ERR_INVALID_ARG, "unknown schedule %d", g->schedule);
@@ -674,7 +676,11 @@ int stencil_step_common(const sgb_grid *g, const void *u_cur, void *u_prev_to_ne
     sgb_layout_info L;
     int rc = check_grid(g, &L);
     if (rc) return rc;
-    const bool diff = g->storage == SGB_FP32_DIFF || g->storage == SGB_BF16_DIFF;
+    const bool diff = g->storage == SGB_FP32_DIFF || g->storage == SGB_BF16_DIFF ||
+                      g->storage == SGB_FP16_DIFF;
+    if (g->storage == SGB_FP16_DIFF)
+        return fail(SGB_ERR_INVALID_ARG,
+                    "stencil_step: SGB_FP16_DIFF keeps scale states for u and d (run_shot only)");
     if (diff && !d_io)
         return fail(SGB_ERR_INVALID_ARG,
                     "stencil_step: the difference-form storage keeps a third field; use "
@@ -1077,10 +1083,15 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
         CUDA_TRY(cudaGetLastError());
         t_launches += 3;
     }
+    ScaleState *ssd = nullptr;  // difference form: the scales of d
     if (Elem<T>::SCALED) {
-        if ((rc = sc.get((void **)&ss, sizeof(ScaleState)))) return rc;
         static const ScaleState init = {{1.0f, 1.0f, 1.0f, 1.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+        if ((rc = sc.get((void **)&ss, sizeof(ScaleState)))) return rc;
         CUDA_TRY(cudaMemcpyAsync(ss, &init, sizeof init, cudaMemcpyHostToDevice, st));
+        if (DIFF) {
+            if ((rc = sc.get((void **)&ssd, sizeof(ScaleState)))) return rc;
+            CUDA_TRY(cudaMemcpyAsync(ssd, &init, sizeof init, cudaMemcpyHostToDevice, st));
+        }
     }
     make_m_kernel<<<ew_grid(ncomp, *ds), 256, 0, st>>>(pad_geom(L), d_vel, g->dt, m);
     CUDA_TRY(cudaGetLastError());
@@ -1094,6 +1105,7 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     base.phi = phi;
     base.err = d_err;
     base.scale = ss;
+    base.scale_d = ssd;
     if (src_ijk) {
         base.si = src_ijk[0];
         base.sj = src_ijk[1];
@@ -1107,7 +1119,9 @@ int run_shot_t(const sgb_grid *g, const sgb_layout_info &L, DevState *ds, cudaSt
     base.traces = d_tr;
     base.rec_n0 = n_begin;
     base.d_io = dfield;
-    const int occ = DIFF ? (std::is_same<T, float>::value ? ds->occ_df : ds->occ_db)
+    const int occ = DIFF ? (std::is_same<T, float>::value    ? ds->occ_df
+                            : std::is_same<T, __half>::value ? ds->occ_dh
+                                                             : ds->occ_db)
                     : std::is_same<T, float>::value ? ds->occ
                     : std::is_same<T, __half>::value ? ds->occ_h : ds->occ_b;
     int grid = 0;
@@ -1525,6 +1539,10 @@ int run_shot_common(const sgb_grid *g, const float *velocity, const float *wavel
         rc = run_shot_t<__nv_bfloat16, true>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end,
                                              src_ijk, rec_ijk, nrec, d_off, d_tr, final_u, dst,
                                              d_err);
+        break;
+    case SGB_FP16_DIFF:
+        rc = run_shot_t<__half, true>(g, L, ds, st, sc, d_vel, d_wav, n_begin, n_end, src_ijk,
+                                      rec_ijk, nrec, d_off, d_tr, final_u, dst, d_err);
         break;
     default:
         // temporal blocking covers whole shots; a segment takes one step per launch

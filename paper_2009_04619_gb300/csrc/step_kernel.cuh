@@ -114,6 +114,7 @@ struct StepArgs {
     const long long *rec_off;
     float *traces;
     ScaleState *scale;     // fp16 storage only
+    ScaleState *scale_d;   // fp16 storage in MODE_DIFF: scales and maxima of d
     float *acc_out;        // MODE_FWD_ACC: g = L u^n + phi^n + f^n (padded fp32)
     float *gsum;           // MODE_ADJ: fp32 partial sum of w^k g^{k-1} (padded)
     const float *mu_in;    // MODE_ADJ: mu^{k+1} (padded); phi is mu^k
@@ -408,7 +409,8 @@ struct StepCta {
     int useq, pseq;  // FLOW: u and (u^{n-1}, m, phi) planes of earlier units of this CTA
     void *u_out_v;   // FLOW, PARITY: the output buffer of the current step
     float s_cur, s_prev, inv_s_next;  // fp16 scales (1 otherwise)
-    float vmax;                       // running max |u^{n+1}| of this thread
+    float sd_cur, inv_sd_next;        // fp16 MODE_DIFF: scales of d^n and d^{n+1}
+    float vmax, vmax_d;               // running max |u^{n+1}|, |d^{n+1}| of this thread
     // PML terms of the thread's fixed columns i = gi + e and rows j = gj0 + r:
     // eta dt = a d(i)^2, the gradient factor k (d(i+1)^2 - d(i-1)^2), the
     // adjoint's k G(i +- 1) with G(y) = d(y+1)^2 - d(y-1)^2, and PML masks
@@ -657,7 +659,7 @@ struct StepCta {
             if constexpr (SCALED) {  // stored values -> true values
                 Lr = f4mul(s_cur, Lr);
                 c = f4mul(s_cur, c);
-                up = f4mul(s_prev, up);
+                up = f4mul(MODE == MODE_DIFF ? sd_cur : s_prev, up);
             }
             float4 un;  // MODE_DIFF: d^{n+1} until the source is added
             if constexpr (MODE == MODE_DIFF) {  // up = d^n: d^{n+1} = d^n + m L u^n
@@ -784,6 +786,11 @@ struct StepCta {
                     vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(un.x), fabsf(un.y)),
                                              fmaxf(fabsf(un.z), fabsf(un.w))));
                     un = f4mul(inv_s_next, un);
+                    if constexpr (MODE == MODE_DIFF) {
+                        vmax_d = fmaxf(vmax_d, fmaxf(fmaxf(fabsf(dn.x), fabsf(dn.y)),
+                                                     fmaxf(fabsf(dn.z), fabsf(dn.w))));
+                        dn = f4mul(inv_sd_next, dn);
+                    }
                 }
                 T *uo = static_cast<T *>(OUTV ? u_out_v : a.u_out) + off;
                 const bool wphi = PML && any_pml;  // phi^{n+1}, or mu^k in the adjoint
@@ -1036,14 +1043,29 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     const int nit = st.z1 - st.z0;
     st.n = n;
     st.aborted = false;
-    st.s_cur = st.s_prev = st.inv_s_next = 1.0f;
-    st.vmax = 0.0f;
+    st.s_cur = st.s_prev = st.inv_s_next = st.sd_cur = st.inv_sd_next = 1.0f;
+    st.vmax = st.vmax_d = 0.0f;
     if constexpr (S::SCALED) {
         ScaleState *ss = a.scale;
         st.s_cur = ss->s[n & 3];
         st.s_prev = ss->s[(n - 1) & 3];
         const float inj = a.sk >= 0 ? fabsf(*a.m_src * a.wavelet[n] * a.inv_vol) : 0.0f;
-        const float B = 4.0f * fmaxf(ss->mx[n & 3], ss->mx[(n - 1) & 3]) + inj;
+        float B = 4.0f * fmaxf(ss->mx[n & 3], ss->mx[(n - 1) & 3]) + inj;
+        if constexpr (MODE == MODE_DIFF) {
+            // |m L u| <= 4 max|u| at a stable dt, so |d^{n+1}| <= 2 max|d^n| + 4 max|u^n|
+            // + the injected amplitude (the factor 2 covers the PML terms), and
+            // |u^{n+1}| <= max|u^n| + that
+            ScaleState *sd = a.scale_d;
+            st.sd_cur = sd->s[n & 3];
+            const float Bd = 2.0f * sd->mx[n & 3] + 4.0f * ss->mx[n & 3] + inj;
+            const float sd_next = pow2_scale_for(Bd);
+            st.inv_sd_next = 1.0f / sd_next;  // exact: a power of two
+            B = ss->mx[n & 3] + Bd;
+            if (unit == 0 && tid == 0 && !sample_only) {
+                sd->s[(n + 1) & 3] = sd_next;
+                sd->mx[(n + 2) & 3] = 0.0f;
+            }
+        }
         const float s_next = pow2_scale_for(B);
         st.inv_s_next = 1.0f / s_next;  // exact: a power of two
         if (unit == 0 && tid == 0 && !sample_only) {
@@ -1097,6 +1119,12 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
         for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (st.lane == 0 && v > 0.0f) atomicMax(reinterpret_cast<int *>(&a.scale->mx[(n + 1) & 3]),
                                                  __float_as_int(v));
+        if constexpr (MODE == MODE_DIFF) {  // and max |d^{n+1}|
+            float vd = st.vmax_d;
+            for (int o = 16; o > 0; o >>= 1) vd = fmaxf(vd, __shfl_xor_sync(0xffffffffu, vd, o));
+            if (st.lane == 0 && vd > 0.0f)
+                atomicMax(reinterpret_cast<int *>(&a.scale_d->mx[(n + 1) & 3]), __float_as_int(vd));
+        }
     }
 }
 

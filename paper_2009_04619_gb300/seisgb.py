@@ -34,6 +34,7 @@ BF16 = 2
 # a third wavefield: run_shot and stencil_step_diff
 FP32_DIFF = 3
 BF16_DIFF = 4
+FP16_DIFF = 5  # scaled fp16 in difference form: run_shot only
 
 # run_shot time-loop schedules (sgb_grid.schedule)
 SCHED_AUTO = 0
@@ -265,7 +266,7 @@ def _stream(stream):
 
 
 _WAVE_DTYPE = {FP32: "float32", FP16_SCALED: "float16", BF16: "bfloat16",
-               FP32_DIFF: "float32", BF16_DIFF: "bfloat16"}
+               FP32_DIFF: "float32", BF16_DIFF: "bfloat16", FP16_DIFF: "float16"}
 
 
 def stencil_step(g: Grid, u_cur, u_prev_to_next, m, phi, step: int = 0, source=None,

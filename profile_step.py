@@ -69,7 +69,8 @@ def _storage(a):
     n_in = a.n - 2 * a.nb
     v = 3000.0
     fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16,
-           "fp32_diff": seisgb.FP32_DIFF, "bf16_diff": seisgb.BF16_DIFF}[a.storage]
+           "fp32_diff": seisgb.FP32_DIFF, "bf16_diff": seisgb.BF16_DIFF,
+           "fp16_diff": seisgb.FP16_DIFF}[a.storage]
     g0 = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, 1.0, v)
     dt = float(np.float32(0.4 * seisgb.cfl_dt(g0, v)))
     g = seisgb.make_grid(n_in, n_in, n_in, a.nb, 10.0, 10.0, 10.0, dt, v, storage=fmt)
@@ -140,7 +141,8 @@ def _shots(a):
     scheds = {"step": seisgb.SCHED_STEP, "flow": seisgb.SCHED_FLOW}
     if a.storage:
         fmt = {"fp32": seisgb.FP32, "fp16": seisgb.FP16_SCALED, "bf16": seisgb.BF16,
-           "fp32_diff": seisgb.FP32_DIFF, "bf16_diff": seisgb.BF16_DIFF}[a.storage]
+           "fp32_diff": seisgb.FP32_DIFF, "bf16_diff": seisgb.BF16_DIFF,
+           "fp16_diff": seisgb.FP16_DIFF}[a.storage]
     else:
         fmt = seisgb.FP32
     for name, sched in scheds.items():
@@ -212,7 +214,7 @@ def main(argv=None):
     p.add_argument("--adjoint", action="store_true", help="time one misfit-gradient shot")
     p.add_argument("--nt", type=int, default=200, help="time steps of the gradient shot")
     p.add_argument("--ckpt", type=int, default=100, help="checkpoint interval of the gradient shot")
-    p.add_argument("--storage", choices=["fp32", "fp16", "bf16", "fp32_diff", "bf16_diff"], default=None,
+    p.add_argument("--storage", choices=["fp32", "fp16", "bf16", "fp32_diff", "bf16_diff", "fp16_diff"], default=None,
                    help="time a short run_shot with 16-bit wavefield storage")
     p.add_argument("--serve", type=int, default=0,
                    help="submit this many requests of the serving mix to a server at once")

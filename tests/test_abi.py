@@ -276,7 +276,20 @@ def test_difference_form_storage_checks(lib):
                                   src.ctypes.data, None, 0, None, *[x.ctypes.data for x in st],
                                   None) == seisgb.ERR_INVALID_ARG
         assert "segments need SGB_FP32 or SGB_BF16" in seisgb.last_error()
-    for bad in (-1, 5):
+    g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=seisgb.FP16_DIFF)
+    seisgb.layout(g)
+    E = int(seisgb.layout(g).elems)
+    buf = np.zeros(5 * E + 16, np.float32)
+    b = buf.ctypes.data + (16 - buf.ctypes.data % 16) % 16
+    fld = [b + 4 * E * q for q in range(4)]
+    assert L.stencil_step_diff(ctypes.byref(g), fld[0], fld[1], fld[2], fld[3], fld[3], 0, None,
+                               None, None) == seisgb.ERR_INVALID_ARG
+    assert "run_shot only" in seisgb.last_error()
+    for sched in (seisgb.SCHED_PAIRS, seisgb.SCHED_FLOW):
+        with pytest.raises(seisgb.SeisgbError):
+            seisgb.layout(seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000,
+                                           storage=seisgb.FP16_DIFF, schedule=sched))
+    for bad in (-1, 6):
         g = seisgb.make_grid(8, 8, 8, 2, 10, 10, 10, 1e-3, 3000, storage=bad)
         with pytest.raises(seisgb.SeisgbError):
             seisgb.layout(g)

@@ -70,7 +70,9 @@ def test_difference_form_small_case():
     fp32 bound (2e-5) against the oracle, PML included (measured 2.7e-6 /
     5.2e-7).  In bf16 a stored rounding error of u no longer enters the time
     difference: measured 1.0e-2 / 5.4e-3 against 2.4e-2 / 1.1e-2 for the bf16
-    leapfrog state; the bounds are about 3x the measured errors."""
+    leapfrog state; scaled fp16 in difference form 1.1e-3 / 4.6e-4 against 2.8e-3 /
+    9.8e-4 for the fp16 leapfrog state.  The bounds are about 3x the measured
+    errors."""
     ensure_lib()
     w = synth.SMALL
     vel = w.velocity()
@@ -78,7 +80,7 @@ def test_difference_form_small_case():
     errs = {}
     ref = None
     for name, fmt in (("fp32_diff", seisgb.FP32_DIFF), ("bf16_diff", seisgb.BF16_DIFF),
-                      ("bf16", seisgb.BF16)):
+                      ("bf16", seisgb.BF16), ("fp16_diff", seisgb.FP16_DIFF)):
         tr, u, dt, wav, rec = _run(w, vel, fmt, w.nt, rec)
         if ref is None:
             ref = _oracle(w, vel, dt, wav, rec, w.nt)
@@ -88,6 +90,7 @@ def test_difference_form_small_case():
     assert errs["fp32_diff"][0] <= 2e-5 and errs["fp32_diff"][1] <= 2e-5
     assert errs["bf16_diff"][0] <= 3e-2 and errs["bf16_diff"][1] <= 1.6e-2
     assert errs["bf16_diff"][0] < 0.7 * errs["bf16"][0]
+    assert errs["fp16_diff"][0] <= 3.5e-3 and errs["fp16_diff"][1] <= 1.5e-3
 
 
 def test_fp32_difference_form_ragged_layered_vs_oracle():
@@ -128,13 +131,15 @@ def test_256_cube_1000_steps_error_per_format():
     1.4e-1 / 6.9e-2 and bf16 diverged).  fp32 error grows with the step count:
     2.7e-6 after 100 steps of the small case, 1.8e-4 after 1000 here.  The
     difference form brings bf16 below 1e-1: measured 5.1e-2 / 2.6e-2
-    (BF16_DIFF), and 1.1e-4 / 2.8e-5 for FP32_DIFF."""
+    (BF16_DIFF), and 1.1e-4 / 2.8e-5 for FP32_DIFF; scaled fp16 in difference form
+    6.4e-3 / 3.1e-3 (FP16_DIFF) against 2.2e-2 / 1.3e-2."""
     ensure_lib()
     w = synth.scaled(synth.LARGE, 192, 32, 1000, name="fwd256_pml32_layered_ricker10_nt1000")
     vel = w.velocity()
     errs = {}
     ref = None
-    formats = dict(FORMATS, fp32_diff=seisgb.FP32_DIFF, bf16_diff=seisgb.BF16_DIFF)
+    formats = dict(FORMATS, fp32_diff=seisgb.FP32_DIFF, bf16_diff=seisgb.BF16_DIFF,
+                   fp16_diff=seisgb.FP16_DIFF)
     for name, fmt in formats.items():
         tr, u, dt, wav, rec = _run(w, vel, fmt, w.nt)
         if ref is None:
@@ -146,6 +151,7 @@ def test_256_cube_1000_steps_error_per_format():
     assert errs["bf16"][0] <= 4e-1 and errs["bf16"][1] <= 3e-1
     assert errs["fp32_diff"][0] <= 5e-4 and errs["fp32_diff"][1] <= 5e-4
     assert errs["bf16_diff"][0] <= 1e-1 and errs["bf16_diff"][1] <= 8e-2
+    assert errs["fp16_diff"][0] <= 2e-2 and errs["fp16_diff"][1] <= 1e-2
 
 
 # Stored mantissa bits of the 16-bit formats: fp16 keeps 10, bf16 7.
