@@ -23,7 +23,7 @@ namespace sgb {
 #define SGB_UNROLL 1
 #endif
 #ifndef SGB_NU
-#define SGB_NU 8
+#define SGB_NU 9
 #endif
 #ifndef SGB_NP
 #define SGB_NP 4
