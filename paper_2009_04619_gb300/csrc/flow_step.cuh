@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(C::BLOCK, (min_blocks<C, T>()))
     using S = StepCta<C, T, MODE_FWD, VAR_FLOW>;
     using G = Stage<C, T>;
     static_assert(!S::SCALED, "the dataflow launch has no per-step fp16 scale");
-    constexpr int NU = C::NU, NP = C::NP, THREADS = C::THREADS, TY = C::TY;
+    constexpr int NU = S::NU, NP = S::NP, THREADS = C::THREADS, TY = C::TY;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S st;

@@ -302,9 +302,19 @@ struct Stage {
     // MODE_ADJ: mu^{k+1} one plane below each thread's points, kept from plane to
     // plane in shared memory (registers are at their limit)
     static constexpr int MZ_BYTES = MODE == MODE_ADJ ? C::THREADS * C::TY * 16 : 0;
-    static constexpr size_t SMEM_BYTES = size_t(C::NU) * U_BYTES + size_t(C::NP) * P_BYTES +
-                                         size_t(MZ_BYTES) + size_t(C::NU + C::NP) * 16 +
-                                         size_t(C::NU + C::NP + 1) * 4;
+    // ring depths: 16-bit storage halves the stages' bytes, so its rings run deeper
+    // (12 u^n planes and 6 tile stages in ~108 KB, still two CTAs per SM)
+#ifndef SGB_NU16
+#define SGB_NU16 12
+#endif
+#ifndef SGB_NP16
+#define SGB_NP16 6
+#endif
+    static constexpr int NU = sizeof(T) == 2 ? SGB_NU16 : C::NU;
+    static constexpr int NP = sizeof(T) == 2 ? SGB_NP16 : C::NP;
+    static constexpr size_t SMEM_BYTES = size_t(NU) * U_BYTES + size_t(NP) * P_BYTES +
+                                         size_t(MZ_BYTES) + size_t(NU + NP) * 16 +
+                                         size_t(NU + NP + 1) * 4;
     static_assert(U_BYTES % 128 == 0 && F_BYTES % 128 == 0, "stage alignment");
     static_assert(SW <= 256, "TMA box limit");
 };
@@ -381,7 +391,7 @@ struct StepCta {
     // PML receive psi from their PML neighbours
     static constexpr int BAND = MODE == MODE_ADJ ? 1 : 0;
     static constexpr bool SCALED = E::SCALED;
-    static constexpr int TXT = C::TXT, TY = C::TY, NU = C::NU, NP = C::NP;
+    static constexpr int TXT = C::TXT, TY = C::TY, NU = Stage<C, T, MODE>::NU, NP = Stage<C, T, MODE>::NP;
     static constexpr int THREADS = C::THREADS, QN = C::QN, U = C::U, WARPS = C::WARPS;
     static constexpr int BX = C::BX, BY = C::BY, HX = G::HX, SW = G::SW;
     static constexpr int P_TILE = C::P_TILE;
@@ -992,7 +1002,7 @@ __device__ __forceinline__ void step_unit(const StepArgs &a, const StepMapPtrs &
     using G = Stage<C, T, MODE>;
     static_assert(MODE == MODE_FWD || MODE == MODE_DIFF || sizeof(T) == 4,
                   "the adjoint runs in fp32");
-    constexpr int TY = C::TY, NU = C::NU, NP = C::NP, THREADS = C::THREADS;
+    constexpr int TY = C::TY, NU = G::NU, NP = G::NP, THREADS = C::THREADS;
     constexpr int BX = C::BX, BY = C::BY;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
