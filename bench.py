@@ -42,8 +42,8 @@ HBM_FALLBACK_GBS = 6800.0
 # kernel source it was measured on (comments and whitespace removed); a
 # changed kernel reports null.
 NCU_TRAFFIC = {
-    # ncu on the 512^3 + 32-point-PML step: 1.953 GB read + 0.678 GB written per launch
-    "433bea5d31005e4c": 2.631e9,
+    # ncu on the 512^3 + 32-point-PML step: 1.959 GB read + 0.678 GB written per launch
+    "c661d56f6bfa4b42": 2.638e9,
 }
 
 
