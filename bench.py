@@ -60,7 +60,7 @@ def _args():
                    help="shot requests in the serving leg (0: skip)")
     p.add_argument("--grad-shots", type=int, default=16,
                    help="shots of the adjoint-gradient leg (0: skip)")
-    p.add_argument("--grad-workers", type=int, default=4,
+    p.add_argument("--grad-workers", type=int, default=8,
                    help="gradient shots in flight at once (host threads, one stream each)")
     p.add_argument("--oracle-steps", type=int, default=40,
                    help="time steps per oracle sample (CPU baseline / reference arm)")
@@ -280,9 +280,10 @@ def _gradient(a, seisgb, synth, peak, uuid=None):
     against traces of the unperturbed model, gradients summed over the shots
     (fp64); shots/s, forward-equivalent Gpt/s and the whole computation's
     algorithmic bytes per second against the HBM peak.  Each rank keeps
-    `--grad-workers` shots in flight on as many streams (host threads; 4 by
-    default, which divides the 16 shots evenly); under torchrun the shots are
-    split across ranks and one fp64 all-reduce sums the gradients."""
+    `--grad-workers` shots in flight on as many streams (host threads; 8 by
+    default, which divides the 16 shots evenly, ~16 GB of scratch each); under
+    torchrun the shots are split across ranks and one fp64 all-reduce sums the
+    gradients."""
     import torch
     from paper_2009_04619_gb300 import replicas
     rank, world, _ = _dist()
