@@ -1,5 +1,5 @@
 """Launch the fused step kernel back to back on a synthetic grid and report its
-time per launch (CUDA events) -- a small driver for timing and for ncu captures.
+time per launch (CUDA events) -- a small script for timing and for ncu captures.
 
     python profile_step.py --n 256 --nb 32 --launches 20
     python profile_step.py --adjoint --n 256 --nb 16 --nt 200
